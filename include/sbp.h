@@ -1,0 +1,176 @@
+/*
+ * sbp.h — C ABI of the GB300 shearing-box Poisson solver (VGF-HybridBC).
+ *
+ * Solves ∇²Φ = 4πGρ (arXiv 2510.10070, Eq. Poisson) on a Cartesian box with
+ * shear-periodic horizontal and vacuum vertical boundary conditions, by the
+ * discrete-Green's-function spectral method of Sect. 2.3:
+ *
+ *   Φ = 4πG F⁻¹( Ĝ^L(k(t), k_z) · F(ρ zero-padded to 2·nz in z) ),
+ *
+ * truncated back to the physical cells, where F is the 3D DFT, k(t) is the
+ * sheared horizontal wave-vector of Sect. 2.1 and Ĝ^L is Eq. (Green's
+ * function regularized in Fourier) with L = Lz.  The density is taken in the
+ * periodic (remapped) frame at shear time t and the potential is returned in
+ * the same frame (step 2 of the three-step scheme of Sect. 2.1).
+ *
+ * Conventions used by every call:
+ *   - rho and phi are DEVICE pointers to dense C-order arrays [nz][ny][nx]
+ *     (x fastest) of double (SBP_F64) or float (every other dtype).
+ *   - Cells are cell-centred; the vertical window is [-Lz/2, Lz/2].
+ *   - The output is the real part of the complex solve, i.e. the multiplier
+ *     is ½[Ĝ(k) + Ĝ(k of the Hermitian partner)], which differs from Ĝ only
+ *     on the Nyquist planes of a sheared box.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Every call is asynchronous on that stream; the caller synchronises.
+ *   - Nothing here calls exit() or traps: failures come back as sbp_status.
+ *
+ * Ownership: the caller owns rho and phi.  A plan owns its device workspace
+ * (the half spectrum, (nx/2+1)·ny·nz complex values, plus small tables), which
+ * it allocates in sbp_plan_create and frees in sbp_plan_destroy.  One solve
+ * may be in flight per plan; use one plan per stream.
+ */
+#ifndef SBP_H
+#define SBP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sbp_plan_s* sbp_plan;
+
+/* Arithmetic of the FFT passes.  SBP_F64: everything in FP64.  SBP_F32: FP32
+ * passes; FP64 Green's parameters, FP64-derived twiddles, and an FP64 k = 0
+ * (mean-mode) side path.  The split dtypes are reserved for tensor-core
+ * radix stages and are rejected with SBP_ERR_UNSUPPORTED_DTYPE. */
+typedef enum {
+    SBP_F64 = 0,
+    SBP_F32 = 1,
+    SBP_F32_SPLIT_F16 = 2,
+    SBP_F32_SPLIT_BF16 = 3
+} sbp_dtype;
+
+typedef enum {
+    SBP_OK = 0,
+    SBP_ERR_INVALID_ARG = 1,       /* NULL/unaligned/partially overlapping pointer, bad number */
+    SBP_ERR_UNSUPPORTED_SIZE = 2,  /* a dimension outside the supported lengths */
+    SBP_ERR_OUT_OF_MEMORY = 3,     /* device allocation failed */
+    SBP_ERR_CUDA = 4,              /* a CUDA runtime call or kernel launch failed */
+    SBP_ERR_DEVICE_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    SBP_ERR_NOT_SAME_DTYPE = 6,    /* batched call mixing dtypes */
+    SBP_ERR_UNSUPPORTED_DTYPE = 7  /* dtype not built in this library */
+} sbp_status;
+
+/* Plan stages that sbp_run_stage can run alone (see there). */
+typedef enum {
+    SBP_STAGE_X_FORWARD = 0,
+    SBP_STAGE_Y_FORWARD = 1,
+    SBP_STAGE_Z_CONVOLVE = 2,
+    SBP_STAGE_Y_INVERSE = 3,
+    SBP_STAGE_X_INVERSE = 4,
+    SBP_STAGE_GREEN_TABLE = 5
+} sbp_stage;
+
+/*
+ * sbp_plan_create — validate a box, build its tables and allocate workspace.
+ *
+ * Sect. 2.1 and 2.3.  nx, ny: horizontal cells, each even and ≥ 4; nz ≥ 2
+ * vertical cells (zero-padded to 2·nz inside the solve).  Each of nx, ny and
+ * nz must be 2^a or 3·2^a, and nx, ny, nz ≤ 2048; other sizes return
+ * SBP_ERR_UNSUPPORTED_SIZE.  Lx, Ly, Lz > 0: box lengths.  q, Omega: shear
+ * rate q·Ω in Δy0(t) = mod(q Ω Lx t, Ly) (the paper's q is 3/2); Omega > 0,
+ * q finite.  G > 0: gravitational constant.  dtype: see sbp_dtype.
+ * The plan binds to the CUDA device that is current at creation.
+ * On failure *out is set to NULL and nothing is leaked.
+ */
+sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz,
+                           double Lx, double Ly, double Lz,
+                           double q, double Omega, double G, sbp_dtype dtype);
+
+/*
+ * sbp_solve — one solve at shear time t (finite).
+ *
+ * Sect. 2.3, Eq. (Green's function regularized in Fourier) and the closing
+ * convolution Φ = 4πG F⁻¹(Ĝ^L·ρ̂).  rho: device input (see conventions);
+ * phi: device output of the same shape and type.  phi == rho (in place) is
+ * allowed; any other overlap returns SBP_ERR_INVALID_ARG.  Both pointers must
+ * be 16-byte aligned.  Runs five kernels on `stream`: x forward (real to half
+ * spectrum), y forward, the fused padded z pass (Green's multiply), y inverse,
+ * x inverse.
+ */
+sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* stream);
+
+/*
+ * sbp_solve_batched — nbox independent solves on one stream.
+ *
+ * Each box i is solved exactly as sbp_solve(plans[i], rho[i], phi[i], t[i]).
+ * All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE) and the device.
+ * A plan may appear only once per call.  plans, rho, phi and t are HOST arrays
+ * of length nbox; rho[i] and phi[i] are device pointers.
+ */
+sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const* rho,
+                             void* const* phi, const double* t, void* stream);
+
+/* sbp_plan_destroy — free a plan's device memory.  NULL-safe.  Synchronises
+ * the plan's device before freeing so that no in-flight solve is cut off. */
+void sbp_plan_destroy(sbp_plan p);
+
+/* sbp_status_string — static English text for a status code. */
+const char* sbp_status_string(sbp_status s);
+
+/* Plan options for sbp_plan_set_option. */
+enum {
+    /* Kernel variant of the fused z pass (same result, different speed):
+     * 0 = automatic (the default); 1 = 8 elements per thread, even/odd padded
+     * halves in one thread; 2 = 8 elements per thread, halves in two thread
+     * groups; 3 = one pruned length-2nz transform per column; 4 = even/odd
+     * halves in two thread groups with the default elements per thread.
+     * Variants 1-3 exist for the common lengths only
+     * (SBP_ERR_UNSUPPORTED_SIZE otherwise, plan unchanged). */
+    SBP_OPT_Z_VARIANT = 1
+};
+
+/* sbp_plan_set_option — set a plan option (see the enum above).  Unknown
+ * options or values return SBP_ERR_INVALID_ARG.  Not to be called while a
+ * solve of this plan is in flight. */
+sbp_status sbp_plan_set_option(sbp_plan p, int option, double value);
+
+/* sbp_plan_info — sizes of a plan.  Any output pointer may be NULL.
+ * spectrum_pitch: complex elements per (z, y) row of the half spectrum
+ * (≥ nx/2+1); workspace_bytes: device bytes the plan holds. */
+sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
+                         int* spectrum_pitch, size_t* workspace_bytes);
+
+/*
+ * sbp_run_stage — run one stage of the solve alone, for stage-level tests.
+ *
+ * Layouts ("spectrum" = complex [nz][ny][spectrum_pitch], interleaved re/im
+ * of the plan's real type, entries a ≥ nx/2+1 of each row unused):
+ *   SBP_STAGE_X_FORWARD : in = real [nz][ny][nx], out = spectrum holding
+ *                         X[z][y][a] = Σ_x ρ e^{-2πi a x/nx}, a ≤ nx/2.
+ *   SBP_STAGE_Y_FORWARD : in = out = spectrum (in place, in must equal out);
+ *                         DFT over y with e^{-2πi b y/ny}.
+ *   SBP_STAGE_Z_CONVOLVE: in = out = spectrum; for each column (b, a) the
+ *                         padded vertical convolution with the Green's kernel
+ *                         at shear time t, scaled by 4πG/(nx·ny·2nz).  For
+ *                         SBP_F32 the (0,0) column is left to the FP64 mean
+ *                         mode and written as zero.
+ *   SBP_STAGE_Y_INVERSE : in = out = spectrum; DFT over y with e^{+2πi b y/ny}.
+ *   SBP_STAGE_X_INVERSE : in = spectrum, out = real [nz][ny][nx]; the
+ *                         half-spectrum inverse x DFT (real part, unscaled).
+ *   SBP_STAGE_GREEN_TABLE: in ignored, out = double [ny][nx/2+1][4] holding
+ *                         (k², 1 - e^{-kL}, k_p², 1 - e^{-k_p L}) for each
+ *                         stored mode and its Hermitian partner at time t.
+ * The FP32 mean-mode side path is not part of any single stage.
+ */
+sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream);
+
+/* sbp_version — library version string. */
+const char* sbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBP_H */

@@ -23,6 +23,7 @@ from .vgf import (  # noqa: F401
     vertical_kernel,
     dft_x,
     dft_y,
+    inverse_dft_x_half,
     horizontal_dft,
     inverse_horizontal_dft,
     vertical_convolve,

@@ -55,6 +55,7 @@ __all__ = [
     "vertical_kernel",
     "dft_x",
     "dft_y",
+    "inverse_dft_x_half",
     "horizontal_dft",
     "inverse_horizontal_dft",
     "vertical_convolve",
@@ -217,6 +218,22 @@ def dft_y(X, sign: float = -1.0):
     return np.einsum("by,...ya->...ba", F, X)
 
 
+def inverse_dft_x_half(X, nx: int):
+    """Real rows from a half spectrum X[..., a], a ≤ nx/2, by the Hermitian sum.
+
+    φ[x] = Σ_{a=0}^{nx-1} X̃[a] exp(+2πi a x/nx) with X̃[a] = X[a] for a ≤ nx/2
+    and X̃[a] = conj(X[nx-a]) above; the a = 0 and a = nx/2 terms use their
+    real parts only (they are real for any Hermitian spectrum).  Unscaled.
+    """
+    h = nx // 2 + 1
+    X = np.array(X[..., :h], dtype=np.complex128)
+    X[..., 0] = X[..., 0].real
+    X[..., nx // 2] = X[..., nx // 2].real
+    full = np.concatenate([X, np.conj(X[..., 1:nx // 2][..., ::-1])], axis=-1)
+    F = _dft_matrix(nx, +1.0)  # [x, a]
+    return (full @ F.T).real
+
+
 def horizontal_dft(rho):
     """R[j, b, a] = Σ_{y,x} ρ[j, y, x] exp(-2πi (a x/nx + b y/ny)) over all (a, b)."""
     rho = np.asarray(rho, dtype=np.float64)
@@ -237,13 +254,13 @@ def vertical_convolve(c, R):
     """Φ̂[i, ...] = Σ_{j<nz} c_{i-j}[...] R[j, ...] (linear Toeplitz sum).
 
     ``c`` has shape [2nz-1, ...] (row n + nz - 1 = c_n); ``R`` has [nz, ...].
+    For each output row i the sum over j is one vectorised product-sum.
     """
     nz = R.shape[0]
     out = np.zeros(R.shape, dtype=np.result_type(c, R))
+    j = np.arange(nz)
     for i in range(nz):
-        acc = out[i]
-        for j in range(nz):
-            acc += c[i - j + nz - 1] * R[j]
+        out[i] = np.sum(c[i - j + nz - 1] * R, axis=0)
     return out
 
 

@@ -1,0 +1,669 @@
+// sbp_api.cu — plans, plan-time tables, launch configuration and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/sbp.h"
+
+#include <type_traits>
+#include "sbp_internal.h"
+
+using namespace sbp;
+
+namespace sbp {
+// ---------------------------------------------------------------------------
+// Green's parameter table (stage-level testing): out[b][a][4].
+// ---------------------------------------------------------------------------
+__global__ void k_green_table(double* __restrict__ out, int nx, int ny, double Lx, double Ly, double L, double s) {
+    const int h = nx / 2 + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= h * ny) return;
+    const int b = q / h, a = q - b * h;
+    const GreenMode g = green_mode(a, b, nx, ny, Lx, Ly, L, s);
+    out[4 * q + 0] = g.k2a;
+    out[4 * q + 1] = g.omEa;
+    out[4 * q + 2] = g.k2b;
+    out[4 * q + 3] = g.omEb;
+}
+
+}  // namespace sbp
+
+namespace {
+
+constexpr int kMaxLen = 2048;
+constexpr size_t kSmemBudget = 224 * 1024;  // under the 227 KB opt-in limit, leaving room for static smem
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+bool supported_len(int n) {
+    if (n < 2 || n > kMaxLen) return false;
+    if (is_pow2(n)) return true;
+    return n % 3 == 0 && is_pow2(n / 3);
+}
+
+bool build_fft_plan(int n, int E, FftPlan& P) {
+    std::memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.E = E;
+    if (n % P.E != 0) return false;
+    P.Tf = n / P.E;
+    int rem = n, ns = 1, s = 0;
+    while (rem > 1) {
+        const int r = pick_radix(P.E, rem);  // the same choice as the compile-time plans
+        if (r == 0 || s >= kMaxStages) return false;
+        P.radix[s] = r;
+        P.ns[s] = ns;
+        P.tws[s] = n / (ns * r);
+        ns *= r;
+        rem /= r;
+        ++s;
+    }
+    P.nstage = s;
+    return true;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct PassCfg {
+    int E = 0, C = 0, threads = 0;
+    size_t smem = 0;
+    dim3 grid;
+};
+
+}  // namespace
+
+struct sbp_plan_s {
+    int nx = 0, ny = 0, nz = 0;
+    double Lx = 0, Ly = 0, Lz = 0, q = 0, Omega = 0, G = 0;
+    sbp_dtype dtype = SBP_F64;
+    int device = 0;
+    int pitch = 0, h = 0;
+    size_t rsize = 0;  // bytes per real
+    FftPlan px{}, py{}, pz{};
+    PassCfg xf, xi, yp, zp;
+    int z_variant = 0;         // see SBP_OPT_Z_VARIANT
+    bool z_padded = false;     // the chosen kernel takes the length-2nz twiddle table
+    void* z_fn = nullptr;      // the z-pass kernel of the chosen variant
+    int green_blocks = 0;      // x-forward blocks that fill the Green's table
+    // device memory
+    void* W = nullptr;        // half spectrum
+    void* tables = nullptr;   // twiddles, kz², c00, tile sums, vk0
+    size_t W_bytes = 0, tables_bytes = 0;
+    void* tw_x = nullptr;
+    void* tw_y = nullptr;
+    void* tw_z = nullptr;
+    void* tw_2z = nullptr;
+    void* tw_M = nullptr;      // e^{-2πi k/(2nz)}, k < 2nz
+    void* kz2 = nullptr;
+    double* c00 = nullptr;
+    double* tile_sums = nullptr;
+    double* vk0 = nullptr;    // FP64 mean-mode potential per plane (FP32 path)
+    void* green = nullptr;    // GreenT<T>[ny][nx/2+1] for the current solve
+};
+
+namespace {
+
+bool f64_of(const sbp_plan_s* p) { return p->dtype == SBP_F64; }
+
+template <typename T>
+size_t zpass_smem(int n, int C) {
+    const size_t cs = sizeof(cpx<T>);
+    const size_t kz2_bytes = align_up((size_t)(n + 1) * sizeof(T), 16);
+    const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
+    return 2 * n * cs + kz2_bytes + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
+}
+
+template <typename T>
+size_t zpad_smem(int n, int C) {
+    const size_t cs = sizeof(cpx<T>);
+    const size_t kz2_bytes = align_up((size_t)(n + 1) * sizeof(T), 16);
+    const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
+    return 2 * (size_t)n * cs + kz2_bytes + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
+}
+
+template <typename T>
+size_t ypass_smem(int n, int C) {
+    return (size_t)n * sizeof(cpx<T>) + (size_t)n * xstride(C) * sizeof(cpx<T>);
+}
+
+template <typename T>
+size_t xfwd_smem(int n, int C) {
+    return (size_t)n * sizeof(cpx<T>) + (size_t)C * padded_row(n) * sizeof(cpx<T>);
+}
+
+template <typename T>
+size_t xinv_smem(int n, int C) {
+    return (size_t)n * sizeof(cpx<T>) + (size_t)C * padded_row(n) * sizeof(cpx<T>);
+}
+
+// z-pass variant (SBP_OPT_Z_VARIANT): 0 = automatic (3 where built, else 4);
+// 1 = E = 8 with joint halves; 2 = E = 8 with split halves; 3 = one padded
+// length-2nz transform per column; 4 = plan_E with split halves (every
+// length).  Returns false, leaving the plan unchanged, when the variant does
+// not exist for this length or does not fit.
+template <typename T>
+bool configure_z(sbp_plan_s* p, int variant) {
+    const bool f64 = std::is_same<T, double>::value;
+    const int cmax = f64 ? 8 : 16;
+    if (variant == 0) return configure_z<T>(p, 3) || configure_z<T>(p, 4);
+    int E = plan_E(p->nz, f64);
+    bool joint = false, padded = false;
+    ZKernel<T> fn = nullptr;
+    if (variant == 4) {
+        fn = kernels_for<T>(p->nz, E).z;
+    } else if (variant == 1 || variant == 2) {
+        E = 8;
+        joint = (variant == 1);
+        fn = zvariant_for<T>(p->nz, E, joint);
+    } else if (variant == 3) {
+        padded = true;
+        fn = zpad_for<T>(p->nz, &E);
+    }
+    if (!fn) return false;
+    FftPlan P;
+    if (!build_fft_plan(padded ? 2 * p->nz : p->nz, E, P)) return false;
+    const int per_col = (padded || joint ? 1 : 2) * P.Tf;
+    auto smem = [&](int C) { return padded ? zpad_smem<T>(p->nz, C) : zpass_smem<T>(p->nz, C); };
+    int C = std::max(1, std::min(cmax, kMaxThreads / per_col));
+    C = std::min(C, p->h);
+    while (C > 1 && smem(C) > kSmemBudget) --C;
+    if (C * per_col > kMaxThreads || smem(C) > kSmemBudget) return false;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p->pz = P;
+    p->zp.E = E;
+    p->zp.C = C;
+    p->zp.threads = C * per_col;
+    p->zp.smem = smem(C);
+    p->zp.grid = dim3((unsigned)((p->h + C - 1) / C), (unsigned)p->ny, 1);
+    p->z_variant = variant;
+    p->z_padded = padded;
+    p->z_fn = reinterpret_cast<void*>(fn);
+    return true;
+}
+
+template <typename T>
+bool configure(sbp_plan_s* p) {
+    const bool f64 = std::is_same<T, double>::value;
+    const int cmax = f64 ? 8 : 16;
+    // x passes: C row pairs per block, C | ny/2, threads ≤ kMaxThreads
+    {
+        const int Tf = p->px.Tf;
+        int C = std::max(1, std::min(cmax, kMaxThreads / Tf));
+        while (C > 1 && ((p->ny / 2) % C != 0 || xinv_smem<T>(p->nx, C) > kSmemBudget)) --C;
+        if ((p->ny / 2) % C != 0) return false;
+        const long long pairs = (long long)p->nz * p->ny / 2;
+        p->xf.E = p->xi.E = p->px.E;
+        p->xf.C = p->xi.C = C;
+        p->xf.threads = p->xi.threads = C * Tf;
+        p->xf.smem = xfwd_smem<T>(p->nx, C);
+        p->xi.smem = xinv_smem<T>(p->nx, C);
+        p->xf.grid = p->xi.grid = dim3((unsigned)(pairs / C), 1, 1);
+        if (p->xf.threads > kMaxThreads || p->xi.smem > kSmemBudget) return false;
+    }
+    // y passes: C columns per block
+    {
+        const int Tf = p->py.Tf;
+        int C = std::max(1, std::min(cmax, kMaxThreads / Tf));
+        C = std::min(C, p->h);
+        while (C > 1 && ypass_smem<T>(p->ny, C) > kSmemBudget) --C;
+        p->yp.E = p->py.E;
+        p->yp.C = C;
+        p->yp.threads = C * Tf;
+        p->yp.smem = ypass_smem<T>(p->ny, C);
+        p->yp.grid = dim3((unsigned)((p->h + C - 1) / C), (unsigned)p->nz, 1);
+        if (p->yp.threads > kMaxThreads || p->yp.smem > kSmemBudget) return false;
+    }
+    // Opt in to the full dynamic shared-memory budget for the kernels this
+    // plan uses.  Always the same value, so plans never lower each other's limit.
+    const KernelSet<T> kx = kernels_for<T>(p->nx, p->px.E), ky = kernels_for<T>(p->ny, p->py.E);
+    if (!kx.x_fwd || !ky.y_fwd) return false;
+    const int lim = (int)kSmemBudget;
+    cudaError_t e = cudaFuncSetAttribute(kx.x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kx.x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ky.y_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(ky.y_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    // Green's-table blocks in front of the x-forward grid: one table entry per
+    // thread, so that the FP64 work spreads over as many SMs as possible.
+    p->green_blocks = (p->h * p->ny + p->xf.threads - 1) / p->xf.threads;
+    return e == cudaSuccess && configure_z<T>(p, 0);
+}
+
+// FP64 twiddles e^{-2πi k/n}, k < count, scaled angle step `num/den` of 2π.
+void host_twiddles(std::vector<double>& out, int count, double frac_den) {
+    out.resize(2 * (size_t)count);
+    for (int k = 0; k < count; ++k) {
+        const double ang = kTwoPi * (double)k / frac_den;
+        out[2 * k] = std::cos(ang);
+        out[2 * k + 1] = -std::sin(ang);
+    }
+}
+
+// k = 0 vertical kernel with L = Lz, M = 2nz (Eq. Green's function regularized
+// in Fourier, first two cases, with k_z L = π m):  Ĝ(0,0) = Lz²/2,
+// Ĝ(0, m) = ((-1)^m - 1)/k_z²;  c00_n = (1/M) Σ_m Ĝ(0, m) cos(π m n / nz).
+void host_c00(std::vector<double>& c, int nz, double Lz) {
+    const int M = 2 * nz;
+    c.assign(2 * (size_t)nz - 1, 0.0);
+    for (int n = -(nz - 1); n <= nz - 1; ++n) {
+        double acc = 0.5 * Lz * Lz;
+        for (int m = -nz; m < nz; ++m) {
+            if ((m & 1) == 0) continue;  // even m ≠ 0 contribute zero
+            const double kz = M_PI * (double)m / Lz;
+            const long long ph = ((long long)m * n) % M;
+            acc += (-2.0 / (kz * kz)) * std::cos(M_PI * (double)ph / (double)nz);
+        }
+        c[n + nz - 1] = acc / (double)M;
+    }
+}
+
+template <typename T>
+sbp_status upload_tables(sbp_plan_s* p) {
+    std::vector<double> twx, twy, twz, tw2;
+    host_twiddles(twx, p->nx, p->nx);
+    host_twiddles(twy, p->ny, p->ny);
+    host_twiddles(twz, p->nz, p->nz);
+    host_twiddles(tw2, p->nz, 2.0 * p->nz);  // e^{-πi p/nz}
+    std::vector<double> twM;
+    host_twiddles(twM, 2 * p->nz, 2.0 * p->nz);  // e^{-2πi k/(2nz)}
+    std::vector<double> kz2(p->nz + 1);
+    for (int m = 0; m <= p->nz; ++m) {
+        const double kz = M_PI * (double)m / p->Lz;
+        kz2[m] = kz * kz;
+    }
+    const bool f32 = !f64_of(p);
+    std::vector<double> c00;
+    if (f32) host_c00(c00, p->nz, p->Lz);
+
+    const size_t cs = sizeof(cpx<T>);
+    const int tiles = (int)p->xf.grid.x;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_twx = take(p->nx * cs), o_twy = take(p->ny * cs), o_twz = take(p->nz * cs);
+    const size_t o_tw2 = take(p->nz * cs), o_kz2 = take((p->nz + 1) * sizeof(T));
+    const size_t o_twM = take(2 * (size_t)p->nz * cs);
+    const size_t o_c00 = take((2 * (size_t)p->nz) * sizeof(double));
+    const size_t o_ts = take((size_t)tiles * sizeof(double));
+    const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
+    const size_t o_green = take((size_t)p->h * p->ny * sizeof(GreenT<T>));
+    p->tables_bytes = off;
+    if (cudaMalloc(&p->tables, off) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_OUT_OF_MEMORY;
+    }
+    unsigned char* base = static_cast<unsigned char*>(p->tables);
+    p->tw_x = base + o_twx;
+    p->tw_y = base + o_twy;
+    p->tw_z = base + o_twz;
+    p->tw_2z = base + o_tw2;
+    p->kz2 = base + o_kz2;
+    p->c00 = reinterpret_cast<double*>(base + o_c00);
+    p->tile_sums = reinterpret_cast<double*>(base + o_ts);
+    p->vk0 = reinterpret_cast<double*>(base + o_vk0);
+    p->tw_M = base + o_twM;
+    p->green = base + o_green;
+
+    std::vector<unsigned char> host(off, 0);
+    auto put_cpx = [&](size_t o, const std::vector<double>& v) {
+        T* d = reinterpret_cast<T*>(host.data() + o);
+        for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+    };
+    put_cpx(o_twx, twx);
+    put_cpx(o_twy, twy);
+    put_cpx(o_twz, twz);
+    put_cpx(o_tw2, tw2);
+    put_cpx(o_twM, twM);
+    {
+        T* d = reinterpret_cast<T*>(host.data() + o_kz2);
+        for (int m = 0; m <= p->nz; ++m) d[m] = (T)kz2[m];
+    }
+    if (f32) std::memcpy(host.data() + o_c00, c00.data(), c00.size() * sizeof(double));
+    if (cudaMemcpy(p->tables, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    return SBP_OK;
+}
+
+void free_plan(sbp_plan_s* p) {
+    if (!p) return;
+    if (p->W) cudaFree(p->W);
+    if (p->tables) cudaFree(p->tables);
+    delete p;
+}
+
+double shear_s(const sbp_plan_s* p, double t) {
+    double dy0 = std::fmod(p->q * p->Omega * p->Lx * t, p->Ly);
+    if (dy0 < 0.0) dy0 += p->Ly;
+    if (dy0 >= p->Ly) dy0 -= p->Ly;
+    return dy0 / p->Lx;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            prev = -1;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
+    GreenFill g;
+    g.tab = p->green;
+    const int total = p->h * p->ny;
+    g.per_block = (total + blocks - 1) / blocks;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.Lx = p->Lx;
+    g.Ly = p->Ly;
+    g.L = p->Lz;
+    g.s = shear_s(p, t);
+    return g;
+}
+
+template <typename T>
+XArgs make_xargs(const sbp_plan_s* p) {
+    XArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.P = p->px;
+    a.pitch = p->pitch;
+    a.C = p->xf.C;
+    a.pairs_per_plane = p->ny / 2;
+    a.green_blocks = 0;
+    a.gf.tab = nullptr;
+    a.vk0 = nullptr;
+    return a;
+}
+template <typename T>
+YArgs make_yargs(const sbp_plan_s* p) {
+    YArgs a;
+    a.P = p->py;
+    a.pitch = p->pitch;
+    a.h = p->h;
+    a.C = p->yp.C;
+    return a;
+}
+template <typename T>
+ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
+    ZArgs a;
+    a.P = p->pz;
+    a.pitch = p->pitch;
+    a.h = p->h;
+    a.ny = p->ny;
+    a.C = p->zp.C;
+    a.L = p->Lz;
+    a.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * 2.0 * p->nz);
+    const bool f32 = !f64_of(p);
+    a.zero_k0 = f32 ? 1 : 0;
+    a.green = p->green;
+    a.tile_sums = p->tile_sums;
+    a.tiles_per_plane = (p->ny / 2) / p->xf.C;
+    a.c00 = p->c00;
+    a.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
+    a.vk0 = (f32 && with_k0) ? p->vk0 : nullptr;
+    return a;
+}
+
+// Launch one stage.  `fused` = part of a full solve: the x forward pass also
+// fills the Green's table (and FP32 tile sums), the z pass reduces plane sums
+// and the x inverse pass adds the FP64 mean mode.  Run alone, a stage does
+// only its own transform; the z pass then fills its table first.
+template <typename T>
+sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, double t, cudaStream_t st,
+                        bool fused) {
+    const KernelSet<T> kx = kernels_for<T>(p->nx, p->px.E), ky = kernels_for<T>(p->ny, p->py.E);
+    const bool f32 = !f64_of(p);
+    cpx<T>* W = static_cast<cpx<T>*>(out);
+    switch (stage) {
+        case SBP_STAGE_X_FORWARD: {
+            XArgs a = make_xargs<T>(p);
+            dim3 grid = p->xf.grid;
+            if (fused) {
+                a.green_blocks = p->green_blocks;
+                a.gf = make_green_fill(p, t, p->green_blocks);
+                grid.x += p->green_blocks;
+            }
+            double* sums = (f32 && fused) ? p->tile_sums : nullptr;
+            kx.x_fwd<<<grid, p->xf.threads, p->xf.smem, st>>>(static_cast<const T*>(in), W,
+                                                             static_cast<const cpx<T>*>(p->tw_x), sums, a);
+            break;
+        }
+        case SBP_STAGE_Y_FORWARD:
+            ky.y_fwd<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
+                                                                   make_yargs<T>(p));
+            break;
+        case SBP_STAGE_Z_CONVOLVE:
+            if (!fused) {
+                const int blocks = (p->h * p->ny + 255) / 256;
+                k_green_params<T><<<blocks, 256, 0, st>>>(make_green_fill(p, t, blocks));
+            }
+            reinterpret_cast<ZKernel<T>>(p->z_fn)<<<p->zp.grid, p->zp.threads, p->zp.smem, st>>>(
+                W, static_cast<const cpx<T>*>(p->tw_z),
+                static_cast<const cpx<T>*>(p->z_padded ? p->tw_M : p->tw_2z),
+                static_cast<const T*>(p->kz2), make_zargs<T>(p, fused));
+            break;
+        case SBP_STAGE_Y_INVERSE:
+            ky.y_inv<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
+                                                                   make_yargs<T>(p));
+            break;
+        case SBP_STAGE_X_INVERSE: {
+            XArgs a = make_xargs<T>(p);
+            if (f32 && fused) a.vk0 = p->vk0;
+            kx.x_inv<<<p->xi.grid, p->xi.threads, p->xi.smem, st>>>(
+                static_cast<const cpx<T>*>(in), static_cast<T*>(out), static_cast<const cpx<T>*>(p->tw_x), a);
+            break;
+        }
+        case SBP_STAGE_GREEN_TABLE: {
+            const int total = p->h * p->ny;
+            k_green_table<<<(total + 255) / 256, 256, 0, st>>>(static_cast<double*>(out), p->nx, p->ny, p->Lx,
+                                                             p->Ly, p->Lz, shear_s(p, t));
+            break;
+        }
+        default:
+            return SBP_ERR_INVALID_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? SBP_OK : SBP_ERR_CUDA;
+}
+
+template <typename T>
+sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st) {
+    sbp_status s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true)) != SBP_OK) return s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_Y_FORWARD, p->W, p->W, t, st, true)) != SBP_OK) return s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_Z_CONVOLVE, p->W, p->W, t, st, true)) != SBP_OK) return s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_Y_INVERSE, p->W, p->W, t, st, true)) != SBP_OK) return s;
+    return launch_stage<T>(p, SBP_STAGE_X_INVERSE, p->W, phi, t, st, true);
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+bool aligned16(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0; }
+
+sbp_status check_io(const sbp_plan_s* p, const void* rho, const void* phi, double t) {
+    if (!p || !rho || !phi || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (!aligned16(rho) || !aligned16(phi)) return SBP_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)p->nx * p->ny * p->nz * p->rsize;
+    const uintptr_t r0 = reinterpret_cast<uintptr_t>(rho), f0 = reinterpret_cast<uintptr_t>(phi);
+    if (r0 != f0 && r0 < f0 + bytes && f0 < r0 + bytes) return SBP_ERR_INVALID_ARG;
+    return SBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz, double Lx, double Ly, double Lz, double q,
+                           double Omega, double G, sbp_dtype dtype) {
+    if (!out) return SBP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!finite_pos(Lx) || !finite_pos(Ly) || !finite_pos(Lz) || !finite_pos(Omega) || !finite_pos(G) ||
+        !std::isfinite(q))
+        return SBP_ERR_INVALID_ARG;
+    if (dtype != SBP_F64 && dtype != SBP_F32) {
+        if (dtype == SBP_F32_SPLIT_F16 || dtype == SBP_F32_SPLIT_BF16) return SBP_ERR_UNSUPPORTED_DTYPE;
+        return SBP_ERR_INVALID_ARG;
+    }
+    if (nx < 4 || ny < 4 || nz < 2 || (nx & 1) || (ny & 1)) return SBP_ERR_UNSUPPORTED_SIZE;
+    if (!supported_len(nx) || !supported_len(ny) || !supported_len(nz)) return SBP_ERR_UNSUPPORTED_SIZE;
+
+    sbp_plan_s* p = new (std::nothrow) sbp_plan_s();
+    if (!p) return SBP_ERR_OUT_OF_MEMORY;
+    p->nx = nx;
+    p->ny = ny;
+    p->nz = nz;
+    p->Lx = Lx;
+    p->Ly = Ly;
+    p->Lz = Lz;
+    p->q = q;
+    p->Omega = Omega;
+    p->G = G;
+    p->dtype = dtype;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return SBP_ERR_CUDA;
+    }
+    const bool f64 = (dtype == SBP_F64);
+    p->rsize = f64 ? sizeof(double) : sizeof(float);
+    p->h = nx / 2 + 1;
+    p->pitch = (p->h + 1) / 2 * 2;
+    if (!build_fft_plan(nx, plan_E(nx, f64), p->px) || !build_fft_plan(ny, plan_E(ny, f64), p->py)) {
+        delete p;
+        return SBP_ERR_UNSUPPORTED_SIZE;
+    }
+    const bool ok = f64 ? configure<double>(p) : configure<float>(p);
+    if (!ok) {
+        cudaGetLastError();
+        delete p;
+        return SBP_ERR_UNSUPPORTED_SIZE;
+    }
+    p->W_bytes = (size_t)nz * ny * p->pitch * 2 * p->rsize;
+    if (cudaMalloc(&p->W, p->W_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p->W = nullptr;
+        free_plan(p);
+        return SBP_ERR_OUT_OF_MEMORY;
+    }
+    const sbp_status s = f64 ? upload_tables<double>(p) : upload_tables<float>(p);
+    if (s != SBP_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = p;
+    return SBP_OK;
+}
+
+sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* stream) {
+    const sbp_status v = check_io(p, rho, phi, t);
+    if (v != SBP_OK) return v;
+    DeviceGuard g(p->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return f64_of(p) ? solve_t<double>(p, rho, phi, t, st) : solve_t<float>(p, rho, phi, t, st);
+}
+
+sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const* rho, void* const* phi,
+                             const double* t, void* stream) {
+    if (nbox < 0 || (nbox > 0 && (!plans || !rho || !phi || !t))) return SBP_ERR_INVALID_ARG;
+    for (int i = 0; i < nbox; ++i) {
+        if (!plans[i]) return SBP_ERR_INVALID_ARG;
+        if (plans[i]->dtype != plans[0]->dtype) return SBP_ERR_NOT_SAME_DTYPE;
+        if (plans[i]->device != plans[0]->device) return SBP_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return SBP_ERR_INVALID_ARG;
+        const sbp_status v = check_io(plans[i], rho[i], phi[i], t[i]);
+        if (v != SBP_OK) return v;
+    }
+    for (int i = 0; i < nbox; ++i) {
+        const sbp_status s = sbp_solve(plans[i], rho[i], phi[i], t[i], stream);
+        if (s != SBP_OK) return s;
+    }
+    return SBP_OK;
+}
+
+void sbp_plan_destroy(sbp_plan p) {
+    if (!p) return;
+    {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        free_plan(p);
+    }
+}
+
+const char* sbp_status_string(sbp_status s) {
+    switch (s) {
+        case SBP_OK: return "ok";
+        case SBP_ERR_INVALID_ARG: return "invalid argument";
+        case SBP_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+        case SBP_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case SBP_ERR_CUDA: return "CUDA error";
+        case SBP_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+        case SBP_ERR_NOT_SAME_DTYPE: return "batched plans differ in dtype";
+        case SBP_ERR_UNSUPPORTED_DTYPE: return "dtype not built in this library";
+    }
+    return "unknown status";
+}
+
+sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
+    if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
+    if (option == SBP_OPT_Z_VARIANT) {
+        const int v = (int)value;
+        if ((double)v != value || v < 0 || v > 4) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        const bool ok = f64_of(p) ? configure_z<double>(p, v) : configure_z<float>(p, v);
+        return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
+    }
+    return SBP_ERR_INVALID_ARG;
+}
+
+sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int* spectrum_pitch,
+                         size_t* workspace_bytes) {
+    if (!p) return SBP_ERR_INVALID_ARG;
+    if (nx) *nx = p->nx;
+    if (ny) *ny = p->ny;
+    if (nz) *nz = p->nz;
+    if (dtype) *dtype = (int)p->dtype;
+    if (spectrum_pitch) *spectrum_pitch = p->pitch;
+    if (workspace_bytes) *workspace_bytes = p->W_bytes + p->tables_bytes;
+    return SBP_OK;
+}
+
+sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream) {
+    if (!p || !out || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_TABLE) return SBP_ERR_INVALID_ARG;
+    if (stage != SBP_STAGE_GREEN_TABLE && !in) return SBP_ERR_INVALID_ARG;
+    if ((stage == SBP_STAGE_Y_FORWARD || stage == SBP_STAGE_Z_CONVOLVE || stage == SBP_STAGE_Y_INVERSE) &&
+        in != out)
+        return SBP_ERR_INVALID_ARG;
+    if ((in && !aligned16(in)) || !aligned16(out)) return SBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return f64_of(p) ? launch_stage<double>(p, stage, in, out, t, st, false)
+                     : launch_stage<float>(p, stage, in, out, t, st, false);
+}
+
+const char* sbp_version(void) { return "sbp 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// sbp_internal.h — host-side view of the pass kernels (shared by the
+// instantiation units and the API unit).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sbp_kernels.cuh"
+
+namespace sbp {
+
+template <typename T>
+struct KernelSet {
+    void (*x_fwd)(const T*, cpx<T>*, const cpx<T>*, double*, XArgs) = nullptr;
+    void (*x_inv)(const cpx<T>*, T*, const cpx<T>*, XArgs) = nullptr;
+    void (*y_fwd)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;
+    void (*y_inv)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;
+    void (*z)(cpx<T>*, const cpx<T>*, const cpx<T>*, const T*, ZArgs) = nullptr;  // default z variant
+};
+
+// z-pass variants: elements per thread and joint / split halves.
+template <typename T>
+using ZKernel = void (*)(cpx<T>*, const cpx<T>*, const cpx<T>*, const T*, ZArgs);
+struct ZVariant {
+    int E;
+    bool joint;
+};
+
+// Kernel sets.  Generic sets (runtime length, compile-time elements per
+// thread E) cover every supported length; static sets (compile-time length N)
+// cover the common lengths with a fully unrolled plan.  Each set is defined in
+// one of the sbp_k_*.cu units so that they compile in parallel.
+#define SBP_E_LIST_F32(X) X(float, f32, 2) X(float, f32, 3) X(float, f32, 4) X(float, f32, 6) \
+    X(float, f32, 8) X(float, f32, 12) X(float, f32, 16) X(float, f32, 24)
+#define SBP_E_LIST_F64(X) X(double, f64, 2) X(double, f64, 3) X(double, f64, 4) X(double, f64, 6) \
+    X(double, f64, 8) X(double, f64, 12) X(double, f64, 16)
+#define SBP_N_LIST_F32(X) X(float, f32, 32) X(float, f32, 64) X(float, f32, 96) X(float, f32, 128) \
+    X(float, f32, 192) X(float, f32, 256) X(float, f32, 512) X(float, f32, 1024)
+#define SBP_N_LIST_F64(X) X(double, f64, 32) X(double, f64, 64) X(double, f64, 96) X(double, f64, 128) \
+    X(double, f64, 192) X(double, f64, 256) X(double, f64, 512) X(double, f64, 1024)
+
+#define SBP_DECLARE_SET(T, TAG, E) KernelSet<T> kernels_##TAG##_e##E();
+#define SBP_DECLARE_SET_N(T, TAG, N) KernelSet<T> kernels_##TAG##_n##N();
+SBP_E_LIST_F32(SBP_DECLARE_SET)
+SBP_E_LIST_F64(SBP_DECLARE_SET)
+SBP_N_LIST_F32(SBP_DECLARE_SET_N)
+SBP_N_LIST_F64(SBP_DECLARE_SET_N)
+
+#define SBP_CASE_SET(T, TAG, E) \
+    case E:                     \
+        return kernels_##TAG##_e##E();
+#define SBP_CASE_SET_N(T, TAG, N) \
+    case N:                       \
+        return kernels_##TAG##_n##N();
+
+// Extra static z-pass variants (length N, E, joint), defined next to the
+// static sets; zvariant_for returns null when a variant is not built.
+#define SBP_ZVAR_LIST(X) X(float, f32, 128, 8, 1) X(float, f32, 128, 8, 0) X(float, f32, 256, 8, 1) \
+    X(float, f32, 256, 8, 0) X(float, f32, 64, 8, 1) X(float, f32, 512, 8, 1)
+// Padded z variant (one length-2N transform per column): (type, N, E).
+#define SBP_ZPAD_LIST(X) X(float, f32, 32, 16) X(float, f32, 64, 16) X(float, f32, 96, 24) X(float, f32, 128, 16) \
+    X(float, f32, 192, 24) X(float, f32, 256, 16) X(float, f32, 512, 16) X(double, f64, 32, 8) X(double, f64, 64, 8) \
+    X(double, f64, 128, 8) X(double, f64, 256, 8)
+#define SBP_DECLARE_ZPAD(T, TAG, N, E) ZKernel<T> zpad_##TAG##_n##N();
+SBP_ZPAD_LIST(SBP_DECLARE_ZPAD)
+#define SBP_DEFINE_ZPAD(T, TAG, N, E) \
+    ZKernel<T> zpad_##TAG##_n##N() { return k_z_padded<T, E, N>; }
+
+// Padded z kernel for length n and its elements per thread (null if not built).
+template <typename T>
+inline ZKernel<T> zpad_for(int n, int* E_out) {
+#define SBP_MATCH_ZPAD(TT, TAG, N, EE)                                   \
+    if (std::is_same<T, TT>::value && n == N) {                          \
+        *E_out = EE;                                                     \
+        return reinterpret_cast<ZKernel<T>>(zpad_##TAG##_n##N());        \
+    }
+    SBP_ZPAD_LIST(SBP_MATCH_ZPAD)
+#undef SBP_MATCH_ZPAD
+    return nullptr;
+}
+#define SBP_DECLARE_ZVAR(T, TAG, N, E, J) ZKernel<T> zkernel_##TAG##_n##N##_e##E##_j##J();
+SBP_ZVAR_LIST(SBP_DECLARE_ZVAR)
+#define SBP_DEFINE_ZVAR(T, TAG, N, E, J) \
+    ZKernel<T> zkernel_##TAG##_n##N##_e##E##_j##J() { return k_z_pass<T, E, N, (J != 0)>; }
+
+template <typename T>
+inline ZKernel<T> zvariant_for(int n, int E, bool joint) {
+#define SBP_MATCH_ZVAR(TT, TAG, N, EE, J)                                                   \
+    if (std::is_same<T, TT>::value && n == N && E == EE && joint == (J != 0))               \
+        return reinterpret_cast<ZKernel<T>>(zkernel_##TAG##_n##N##_e##EE##_j##J());
+    SBP_ZVAR_LIST(SBP_MATCH_ZVAR)
+#undef SBP_MATCH_ZVAR
+    return nullptr;
+}
+
+// Kernels for a length-n transform with E elements per thread.
+template <typename T>
+inline KernelSet<T> kernels_for(int n, int E);
+template <>
+inline KernelSet<float> kernels_for<float>(int n, int E) {
+    switch (n) { SBP_N_LIST_F32(SBP_CASE_SET_N) default: break; }
+    switch (E) { SBP_E_LIST_F32(SBP_CASE_SET) default: return KernelSet<float>{}; }
+}
+template <>
+inline KernelSet<double> kernels_for<double>(int n, int E) {
+    switch (n) { SBP_N_LIST_F64(SBP_CASE_SET_N) default: break; }
+    switch (E) { SBP_E_LIST_F64(SBP_CASE_SET) default: return KernelSet<double>{}; }
+}
+
+}  // namespace sbp
+
+#define SBP_SET_BODY(T, E, NS)             \
+    KernelSet<T> s;                        \
+    s.x_fwd = k_x_forward<T, E, NS>;       \
+    s.x_inv = k_x_inverse<T, E, NS>;       \
+    s.y_fwd = k_y_pass<T, E, false, NS>;   \
+    s.y_inv = k_y_pass<T, E, true, NS>;    \
+    s.z = k_z_pass<T, E, NS, false>;       \
+    return s;
+
+// Defines kernels_<TAG>_e<E>() (generic) in the including unit.
+#define SBP_DEFINE_SET(T, TAG, E) \
+    KernelSet<T> kernels_##TAG##_e##E() { SBP_SET_BODY(T, E, 0) }
+// Defines kernels_<TAG>_n<N>() (static length N) in the including unit.
+#define SBP_DEFINE_SET_N(T, TAG, N) \
+    KernelSet<T> kernels_##TAG##_n##N() { SBP_SET_BODY(T, plan_E(N, sizeof(T) == 8), N) }

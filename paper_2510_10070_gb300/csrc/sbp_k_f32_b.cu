@@ -1,0 +1,6 @@
+// sbp_k_f32_b.cu — instantiations of the pass kernels (see sbp_kernels.cuh).
+#include "sbp_internal.h"
+
+namespace sbp {
+SBP_DEFINE_SET(float, f32, 16)
+}  // namespace sbp

@@ -1,0 +1,7 @@
+// sbp_k_f64_n128.cu — static-length instantiations of the pass kernels (see sbp_kernels.cuh).
+#include "sbp_internal.h"
+
+namespace sbp {
+SBP_DEFINE_SET_N(double, f64, 128)
+SBP_DEFINE_ZPAD(double, f64, 128, 8)
+}  // namespace sbp

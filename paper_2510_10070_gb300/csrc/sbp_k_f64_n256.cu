@@ -1,0 +1,7 @@
+// sbp_k_f64_n256.cu — static-length instantiations of the pass kernels (see sbp_kernels.cuh).
+#include "sbp_internal.h"
+
+namespace sbp {
+SBP_DEFINE_SET_N(double, f64, 256)
+SBP_DEFINE_ZPAD(double, f64, 256, 8)
+}  // namespace sbp

@@ -1,0 +1,6 @@
+// sbp_k_f64_n512.cu — static-length instantiations of the pass kernels (see sbp_kernels.cuh).
+#include "sbp_internal.h"
+
+namespace sbp {
+SBP_DEFINE_SET_N(double, f64, 512)
+}  // namespace sbp

@@ -1,0 +1,667 @@
+// sbp_kernels.cuh — the five pass kernels of one VGF-HybridBC solve.
+//
+//   x forward : real rows → half spectrum X[z][y][a], a ≤ nx/2 (r2c by pairing
+//               two real rows into one complex row).
+//   y forward : in place, DFT over y of each (z, a) column.
+//   z pass    : per column (b, a): zero-pad to 2nz, forward DFT, multiply by
+//               4πG/(nx·ny·2nz) · Ĝ_eff(k(t), k_z,m), inverse DFT, keep the
+//               first nz outputs (Sect. 2.3, Eq. Green's function regularized
+//               in Fourier with L = Lz).
+//   y inverse : in place.
+//   x inverse : half spectrum → real rows (c2r by pairing).
+//
+// Spectrum layout: complex [nz][ny][pitch] with pitch ≥ nx/2+1 (even).
+#pragma once
+
+#include <type_traits>
+
+#include "sbp_fft.cuh"
+
+namespace sbp {
+
+constexpr int kMaxThreads = 256;  // threads per block of every pass kernel
+
+// Row stride (complex elements) of a [n][C] exchange buffer: one pad column
+// spreads consecutive rows over the banks; a single column needs none.
+__host__ __device__ constexpr int xstride(int C) { return C == 1 ? 1 : C + 1; }
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+// Green's-function parameters of one stored mode as the z pass reads them.
+template <typename T>
+struct GreenT {
+    T k2a, omEa, k2b, omEb;  // |k|² and 1 - e^{-|k|L}, for the mode and its partner
+    int kzero, same;
+};
+
+// Work a pass kernel may do on the side: fill the Green's table for modes
+// [blockIdx.x·per_block, …) (FP64 arithmetic, rounded to the table type).
+struct GreenFill {
+    void* tab;  // GreenT<T>[ny][nx/2+1] or null
+    int per_block;
+    int nx, ny;
+    double Lx, Ly, L, s;
+};
+
+struct XArgs {
+    FftPlan P;           // length nx
+    int pitch;           // spectrum row pitch (complex elements)
+    int C;               // row pairs per block (divides ny/2)
+    int pairs_per_plane; // ny/2
+    // x forward: the first green_blocks blocks fill the Green's table (FP64)
+    // while the others transform rows
+    int green_blocks;
+    GreenFill gf;
+    // x inverse, FP32 path: FP64 mean-mode potential per plane (null: none)
+    const double* vk0;
+};
+
+struct YArgs {
+    FftPlan P;  // length ny
+    int pitch;
+    int h;      // nx/2 + 1
+    int C;      // columns per block
+};
+
+struct ZArgs {
+    FftPlan P;  // length nz
+    int pitch;
+    int h;
+    int ny;
+    int C;
+    double L;           // L = Lz (enclosure of the truncated Green's function)
+    double scale;       // 4πG / (nx·ny·2nz)
+    int zero_k0;        // FP32 path: leave the (0,0) column to the FP64 side path
+    const void* green;  // GreenT<T>[ny][h] at this solve's time
+    // FP64 mean-mode side path (FP32 path only; vk0 null otherwise): block
+    // (0,0) reduces the x-forward tile sums to plane sums S and convolves them
+    // with the k = 0 kernel: vk0[i] = coef · Σ_j c00[i - j + nz - 1] S[j].
+    const double* tile_sums;
+    int tiles_per_plane;
+    const double* c00;
+    double k0_coef;
+    double* vk0;
+};
+
+// Block (0,0) of a z pass: the FP64 mean mode (O(nz²) FP64 work on one SM,
+// overlapped with the other blocks).  `scratch` holds nz doubles.
+__device__ __forceinline__ void mean_mode_fp64(const ZArgs& A, int nz, double* scratch) {
+    const int tid = threadIdx.x;
+    for (int j = tid; j < nz; j += blockDim.x) {
+        double sacc = 0.0;
+        for (int q = 0; q < A.tiles_per_plane; ++q) sacc += A.tile_sums[(size_t)j * A.tiles_per_plane + q];
+        scratch[j] = sacc;
+    }
+    __syncthreads();
+    for (int i = tid; i < nz; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < nz; ++j) acc = fma(A.c00[i - j + nz - 1], scratch[j], acc);
+        A.vk0[i] = A.k0_coef * acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T fast_div(T a, T b);
+template <>
+__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+template <>
+__device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
+
+// Error-free float sum (Knuth's TwoSum) and double-float accumulation.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    float h, l;
+    two_sum(s, e, h, l);
+    return {h, l};
+}
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e += a.lo;
+    float h, l;
+    two_sum(s, e, h, l);
+    return {h, l};
+}
+
+// Green's-function parameters of stored mode (a, b), a ∈ [0, nx/2], b ∈ [0, ny):
+// |k|² and 1 - e^{-|k| L} for the mode and for its Hermitian partner
+// (Sect. 2.1 wave-vector k_x = K_x + s K_y; Eq. Green's function regularized
+// in Fourier needs e^{-kL}).  FP64 throughout.
+struct GreenMode {
+    double k2a, omEa, k2b, omEb;
+    int kzero;  // signed (a, b) == (0, 0)
+    int same;   // partner has the same |k|
+};
+
+__device__ __forceinline__ int wrap_signed(int v, int n) {
+    if (v >= n / 2) v -= n;
+    if (v < -(n / 2)) v += n;
+    return v;
+}
+
+__device__ __forceinline__ GreenMode green_mode(int a, int b, int nx, int ny, double Lx, double Ly, double L,
+                                                double s) {
+    GreenMode g;
+    const int as = (a < nx / 2) ? a : a - nx;
+    const int bs = (b < ny / 2) ? b : b - ny;
+    const int ap = wrap_signed(-as, nx);
+    const int bp = wrap_signed(-bs, ny);
+    g.kzero = (as == 0 && bs == 0);
+    {
+        const double Kx = kTwoPi * (double)as / Lx, Ky = kTwoPi * (double)bs / Ly;
+        const double kx = fma(s, Ky, Kx);
+        g.k2a = fma(kx, kx, Ky * Ky);
+        g.omEa = g.kzero ? 0.0 : -expm1(-sqrt(g.k2a) * L);
+    }
+    g.same = (ap == -as && bp == -bs);
+    if (g.same) {
+        g.k2b = g.k2a;
+        g.omEb = g.omEa;
+    } else {
+        const double Kx = kTwoPi * (double)ap / Lx, Ky = kTwoPi * (double)bp / Ly;
+        const double kx = fma(s, Ky, Kx);
+        g.k2b = fma(kx, kx, Ky * Ky);
+        g.omEb = -expm1(-sqrt(g.k2b) * L);
+    }
+    return g;
+}
+
+template <typename T>
+__device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
+    if (gf.tab == nullptr) return;
+    GreenT<T>* tab = static_cast<GreenT<T>*>(gf.tab);
+    const int h = gf.nx / 2 + 1;
+    const int total = h * gf.ny;
+    const int q0 = block * gf.per_block;
+    const int q1 = min(total, q0 + gf.per_block);
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+        const int b = q / h, a = q - b * h;
+        const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, gf.s);
+        tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
+    }
+}
+
+// Vectorised contiguous copy global → shared staging (16-byte chunks when the
+// span allows it).  Reals only.
+template <typename T>
+__device__ __forceinline__ void load_rows_to_smem(const T* __restrict__ src, T* __restrict__ tile, int rows, int n,
+                                                  int spitch) {
+    const int total = rows * n;
+    constexpr int V = 16 / sizeof(T);
+    if (n % V == 0) {
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        const V4* s4 = reinterpret_cast<const V4*>(src);
+        for (int q = threadIdx.x; q < total / V; q += blockDim.x) {
+            const V4 w = __ldcs(s4 + q);
+            const int e0 = q * V;
+            const int r = e0 / n, x = e0 - r * n;
+            T* d = tile + r * spitch + x;
+            const T* wv = reinterpret_cast<const T*>(&w);
+#pragma unroll
+            for (int k = 0; k < V; ++k) d[k] = wv[k];
+        }
+    } else {
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int r = q / n, x = q - r * n;
+            tile[r * spitch + x] = src[q];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_rows_from_smem(T* __restrict__ dst, const T* __restrict__ tile, int rows, int n,
+                                                     int spitch) {
+    const int total = rows * n;
+    constexpr int V = 16 / sizeof(T);
+    if (n % V == 0) {
+        using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+        V4* d4 = reinterpret_cast<V4*>(dst);
+        for (int q = threadIdx.x; q < total / V; q += blockDim.x) {
+            const int e0 = q * V;
+            const int r = e0 / n, x = e0 - r * n;
+            const T* s = tile + r * spitch + x;
+            V4 w;
+            T* wv = reinterpret_cast<T*>(&w);
+#pragma unroll
+            for (int k = 0; k < V; ++k) wv[k] = s[k];
+            __stcs(d4 + q, w);
+        }
+    } else {
+        for (int q = threadIdx.x; q < total; q += blockDim.x) {
+            const int r = q / n, x = q - r * n;
+            dst[q] = tile[r * spitch + x];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x forward: C row pairs per block (2C consecutive real rows of one plane).
+// Lanes run along x (t fastest), so each thread loads its E elements of both
+// rows straight from global memory with coalesced loads.
+// smem: tw[n] | C padded rows (exchange, then the paired spectrum Z)
+// ---------------------------------------------------------------------------
+template <typename T, int E, int NS>
+__global__ void __launch_bounds__(kMaxThreads) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
+                                                           const cpx<T>* __restrict__ twg,
+                                                           double* __restrict__ tile_sums, XArgs A) {
+    if ((int)blockIdx.x < A.green_blocks) {  // FP64 Green's table, off the transform blocks
+        green_fill<T>(A.gf, blockIdx.x);
+        return;
+    }
+    const int bid = blockIdx.x - A.green_blocks;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
+    const int RP = padded_row(n);
+    cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* xb = tw + n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) tw[i] = twg[i];
+
+    const int t = tid % Tf, c = tid / Tf;
+    const long long pair0 = (long long)bid * C;
+    const T* r0p = rho + (pair0 + c) * 2 * n;
+    cpx<T> v[1][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = t + Tf * e;
+        v[0][e] = {__ldcs(r0p + x), __ldcs(r0p + n + x)};
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (tile_sums != nullptr) {
+            // FP64-quality plane sums from error-free float additions
+            FF acc = {0.f, 0.f};
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc = ff_add_f(acc, (float)v[0][e].x);
+                acc = ff_add_f(acc, (float)v[0][e].y);
+            }
+            // block reduction; the last warp may be partial, so only lanes
+            // that exist are added
+            const int lane = tid & 31, warp = tid >> 5;
+            const int wl = min(32, (int)blockDim.x - warp * 32);
+            const unsigned mask = (wl == 32) ? 0xffffffffu : ((1u << wl) - 1u);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                FF other = {__shfl_xor_sync(mask, acc.hi, o), __shfl_xor_sync(mask, acc.lo, o)};
+                if ((lane ^ o) < wl) acc = ff_add(acc, other);
+            }
+            __shared__ FF wsum[kMaxThreads / 32];
+            if (lane == 0) wsum[warp] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                FF tot = {0.f, 0.f};
+                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot = ff_add(tot, wsum[w]);
+                tile_sums[bid] = (double)tot.hi + (double)tot.lo;
+            }
+        }
+    }
+    __syncthreads();  // twiddles visible
+    const SmemCol<T> buf[1] = {{xb + c * RP, 0}};
+    fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) buf[0][t + Tf * e] = v[0][e];
+    __syncthreads();
+
+    // split the paired transform: X0 = (Z[k] + conj Z[n-k]) / 2, X1 = -i (Z[k] - conj Z[n-k]) / 2
+    const int h = n / 2 + 1;
+    const T half = (T)0.5;
+    for (int q = tid; q < C * h; q += blockDim.x) {
+        const int cc = q / h, k = q - cc * h;
+        const cpx<T>* zr = xb + cc * RP;
+        const cpx<T> Az = zr[k + (k >> 4)];
+        const int km = (k == 0) ? 0 : n - k;
+        const cpx<T> Bz = cconj(zr[km + (km >> 4)]);
+        const cpx<T> X0 = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
+        const cpx<T> X1 = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
+        const long long row = 2 * (pair0 + cc);
+        W[row * A.pitch + k] = X0;
+        W[(row + 1) * A.pitch + k] = X1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y pass (forward or inverse), in place: block = (a-tile of C columns, plane z).
+// smem: tw[n] | exchange [n][C+1]
+// ---------------------------------------------------------------------------
+template <typename T, int E, bool INV, int NS>
+__global__ void __launch_bounds__(kMaxThreads) k_y_pass(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
+    cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* xb = tw + n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) tw[i] = twg[i];
+
+    const int c = tid % C, t = tid / C;
+    const int a = blockIdx.x * C + c;
+    const bool valid = a < A.h;
+    cpx<T>* col = W + (size_t)blockIdx.y * n * A.pitch + a;
+    cpx<T> v[1][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        cpx<T> x = {(T)0, (T)0};
+        if (valid) x = col[(size_t)(t + Tf * e) * A.pitch];
+        v[0][e] = INV ? cconj(x) : x;
+    }
+    __syncthreads();  // twiddles visible
+    const SmemCol<T> buf[1] = {{xb + c, xstride(C)}};
+    fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+    if (valid) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) col[(size_t)(t + Tf * e) * A.pitch] = INV ? cconj(v[0][e]) : v[0][e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass: block = (a-tile of C columns, row b).  The length-2nz padded DFT of
+// a column x[0..nz) splits into even outputs FFT_nz(x) and odd outputs
+// FFT_nz(x[j]·e^{-πi j/nz}); the truncated inverse recombines
+// y[n] = IFFT_nz(Y_even)[n] + e^{+πi n/nz} IFFT_nz(Y_odd)[n] for n < nz.
+// smem: tw[n] | tw2[n] (e^{-πi p/n}) | kz2[n+1] | green[C] | exchange 2×[n][C+1]
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T green_eff_elem(int m, int nz, T kz2, T k2a, T omEa, T k2b, T omEb, bool kzero,
+                                            bool same, T L2half) {
+    // m ∈ [0, 2nz) unsigned; parity of m equals parity of the signed index.
+    const bool odd = (m & 1) != 0;
+    if (kzero) {
+        if (m == 0) return L2half;
+        return odd ? fast_div((T)-2, kz2) : (T)0;
+    }
+    const T na = odd ? ((T)2 - omEa) : omEa;  // 1 ∓ e^{-kL}
+    T g = -fast_div(na, k2a + kz2);
+    if (!same) {
+        const T nb = odd ? ((T)2 - omEb) : omEb;
+        g = (T)0.5 * (g - fast_div(nb, k2b + kz2));
+    }
+    return g;
+}
+
+// JOINT = true : each thread holds both halves of its E elements (two
+//                 columns of the engine), recombined in registers.
+// JOINT = false: threads come in two halves per column: half 0 carries the
+//                 even padded outputs FFT_n(x), half 1 the odd ones
+//                 FFT_n(x·e^{-πi j/n}); the odd half hands its term over
+//                 through shared memory.
+template <typename T, int E, int NS, bool JOINT>
+__global__ void __launch_bounds__(kMaxThreads) k_z_pass(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg,
+                                                        const cpx<T>* __restrict__ tw2g, const T* __restrict__ kz2g,
+                                                        ZArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
+    const int XS = xstride(C);
+    cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* tw2 = tw + n;
+    T* kz2 = reinterpret_cast<T*>(tw2 + n);
+    const int kz2_slots = ((n + 1) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(kz2 + kz2_slots);
+    const int gm_bytes = ((C * (int)sizeof(GreenT<T>)) + 15) / 16 * 16;
+    cpx<T>* xb0 = reinterpret_cast<cpx<T>*>(reinterpret_cast<unsigned char*>(gm) + gm_bytes);
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) {
+        tw[i] = twg[i];
+        tw2[i] = tw2g[i];
+    }
+    for (int i = tid; i <= n; i += blockDim.x) kz2[i] = kz2g[i];
+    const int b = blockIdx.y;
+    if (tid < C) {
+        const int a = blockIdx.x * C + tid;
+        GreenT<T> g = {};
+        if (a < A.h) g = static_cast<const GreenT<T>*>(A.green)[(size_t)b * A.h + a];
+        gm[tid] = g;
+    }
+    if (A.vk0 != nullptr && blockIdx.x == 0 && blockIdx.y == 0)
+        mean_mode_fp64(A, n, reinterpret_cast<double*>(xb0));
+    __syncthreads();
+
+    constexpr int NH = JOINT ? 2 : 1;  // halves held per thread
+    const int c = tid % C;
+    const int half = JOINT ? 0 : ((tid / C) & 1);
+    const int t = JOINT ? tid / C : tid / (2 * C);
+    const int a = blockIdx.x * C + c;
+    const bool valid = a < A.h;
+    cpx<T>* col = W + (size_t)b * A.pitch + a;
+    const size_t zstride = (size_t)A.ny * A.pitch;
+    cpx<T> v[NH][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int p = t + Tf * e;
+        cpx<T> x = {(T)0, (T)0};
+        if (valid) x = col[(size_t)p * zstride];
+        if constexpr (JOINT) {
+            v[0][e] = x;
+            v[1][e] = cmul(x, tw2[p]);
+        } else {
+            v[0][e] = half ? cmul(x, tw2[p]) : x;
+        }
+    }
+    SmemCol<T> buf[NH];
+    if constexpr (JOINT) {
+        buf[0] = {xb0 + c, XS};
+        buf[1] = {xb0 + (size_t)n * XS + c, XS};
+    } else {
+        buf[0] = {xb0 + (size_t)half * n * XS + c, XS};
+    }
+    fft_run<NS, E, NH, T>(v, t, A.P, tw, buf);
+
+    // multiply by scale·Ĝ_eff(m), m = 2p + half, and conjugate for the inverse
+    {
+        const GreenT<T> g = gm[c];
+        const T scale = (T)A.scale;
+        const T L2half = (T)(0.5 * A.L * A.L);
+        const bool kill = A.zero_k0 && g.kzero;
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int p = t + Tf * e;
+                const int m = 2 * p + (JOINT ? hh : half);
+                const int ms = (m <= n) ? m : 2 * n - m;  // |signed m|
+                const T ge = green_eff_elem<T>(m, n, kz2[ms], g.k2a, g.omEa, g.k2b, g.omEb, g.kzero != 0,
+                                               g.same != 0, L2half);
+                const T f = kill ? (T)0 : ge * scale;
+                v[hh][e] = {v[hh][e].x * f, -v[hh][e].y * f};
+            }
+        }
+    }
+    fft_run<NS, E, NH, T>(v, t, A.P, tw, buf);
+
+    // y[p] = IFFT(Y_even)[p] + e^{+πi p/n} IFFT(Y_odd)[p]
+    if constexpr (JOINT) {
+        if (valid) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int p = t + Tf * e;
+                col[(size_t)p * zstride] = cadd(cconj(v[0][e]), cmul(cconj(v[1][e]), cconj(tw2[p])));
+            }
+        }
+    } else {
+        __syncthreads();
+        if (half) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int p = t + Tf * e;
+                buf[0][p] = cmul(cconj(v[0][e]), cconj(tw2[p]));
+            }
+        }
+        __syncthreads();
+        if (!half && valid) {
+            const SmemCol<T> odd = {xb0 + (size_t)n * XS + c, XS};
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int p = t + Tf * e;
+                col[(size_t)p * zstride] = cadd(cconj(v[0][e]), odd[p]);
+            }
+        }
+    }
+}
+
+// Padded variant: each column is one length-M = 2n transform.  Thread t holds
+// elements t + Tf·e of the padded column; the zero half (e ≥ E/2) never enters
+// the pruned first stage, and of the inverse only the kept half (outputs < n)
+// is stored, so the compiler drops the rest of the last stage.
+// smem: twM[M] | kz2[n+1] | green[C] | exchange [M][xstride(C)]
+template <typename T, int E, int N>
+__global__ void __launch_bounds__(kMaxThreads) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
+                                                          const cpx<T>* __restrict__ twMg, const T* __restrict__ kz2g,
+                                                          ZArgs A) {
+    constexpr int M = 2 * N;
+    constexpr int Tf = M / E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int C = A.C;
+    const int XS = xstride(C);
+    cpx<T>* twM = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* kz2 = reinterpret_cast<T*>(twM + M);
+    constexpr int kz2_slots = ((N + 1) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(kz2 + kz2_slots);
+    const int gm_bytes = ((C * (int)sizeof(GreenT<T>)) + 15) / 16 * 16;
+    cpx<T>* xb = reinterpret_cast<cpx<T>*>(reinterpret_cast<unsigned char*>(gm) + gm_bytes);
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < M; i += blockDim.x) twM[i] = twMg[i];
+    for (int i = tid; i <= N; i += blockDim.x) kz2[i] = kz2g[i];
+    const int b = blockIdx.y;
+    if (tid < C) {
+        const int a = blockIdx.x * C + tid;
+        GreenT<T> g = {};
+        if (a < A.h) g = static_cast<const GreenT<T>*>(A.green)[(size_t)b * A.h + a];
+        gm[tid] = g;
+    }
+    if (A.vk0 != nullptr && blockIdx.x == 0 && blockIdx.y == 0)
+        mean_mode_fp64(A, N, reinterpret_cast<double*>(xb));
+
+    const int c = tid % C, t = tid / C;
+    const int a = blockIdx.x * C + c;
+    const bool valid = a < A.h;
+    cpx<T>* col = W + (size_t)b * A.pitch + a;
+    const size_t zstride = (size_t)A.ny * A.pitch;
+    cpx<T> v[1][E];
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+        cpx<T> x = {(T)0, (T)0};
+        if (valid) x = col[(size_t)(t + Tf * e) * zstride];
+        v[0][e] = x;
+    }
+    const SmemCol<T> buf[1] = {{xb + c, XS}};
+    fft_static_padded<M, E, 1, T>(v, t, twM, buf);  // starts with a barrier: tables are visible
+
+    {
+        const GreenT<T> g = gm[c];
+        const T scale = (T)A.scale;
+        const T L2half = (T)(0.5 * A.L * A.L);
+        const bool kill = A.zero_k0 && g.kzero;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int m = t + Tf * e;
+            const int ms = (m <= N) ? m : M - m;  // |signed m|
+            const T ge = green_eff_elem<T>(m, N, kz2[ms], g.k2a, g.omEa, g.k2b, g.omEb, g.kzero != 0, g.same != 0,
+                                           L2half);
+            const T f = kill ? (T)0 : ge * scale;
+            v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+        }
+    }
+    fft_static<M, E, 0, 1, T>(v, t, twM, buf);
+    if (valid) {
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) col[(size_t)(t + Tf * e) * zstride] = cconj(v[0][e]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x inverse: C row pairs per block, lanes along x.  Each thread assembles
+// Z[k] = X0[k] + i X1[k] (Hermitian extension above nx/2) straight from
+// global memory and stores its real outputs straight back.  Optional FP64
+// mean-mode add (A.vk0 != null).
+// smem: tw[n] | C padded rows (exchange)
+// ---------------------------------------------------------------------------
+template <typename T, int E, int NS>
+__global__ void __launch_bounds__(kMaxThreads) k_x_inverse(const cpx<T>* __restrict__ W, T* __restrict__ phi,
+                                                           const cpx<T>* __restrict__ twg, XArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
+    const int RP = padded_row(n);
+    cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* xb = tw + n;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < n; i += blockDim.x) tw[i] = twg[i];
+
+    const int t = tid % Tf, c = tid / Tf;
+    const long long pair0 = (long long)blockIdx.x * C;
+    const long long row = 2 * (pair0 + c);
+    const cpx<T>* w0 = W + row * A.pitch;
+    const cpx<T>* w1 = w0 + A.pitch;
+    cpx<T> v[1][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = t + Tf * e;
+        cpx<T> z;
+        if (2 * k <= n) {
+            cpx<T> x0 = w0[k], x1 = w1[k];
+            if (k == 0 || 2 * k == n) {
+                x0.y = (T)0;
+                x1.y = (T)0;
+            }
+            z = {x0.x - x1.y, x0.y + x1.x};
+        } else {
+            const cpx<T> x0 = w0[n - k], x1 = w1[n - k];
+            z = {x0.x + x1.y, x1.x - x0.y};
+        }
+        v[0][e] = cconj(z);
+    }
+    __syncthreads();  // twiddles visible
+    const SmemCol<T> buf[1] = {{xb + c * RP, 0}};
+    fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+
+    // mean mode (FP32 path): the FP64 per-plane value, added as a double-float pair
+    T add_hi = (T)0, add_lo = (T)0;
+    const bool addk0 = (A.vk0 != nullptr);
+    if (addk0) {
+        const double vv = A.vk0[pair0 / A.pairs_per_plane];
+        add_hi = (T)vv;
+        add_lo = (T)(vv - (double)add_hi);
+    }
+    T* o0 = phi + row * n;
+    T* o1 = o0 + n;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int x = t + Tf * e;
+        T p0 = v[0][e].x, p1 = -v[0][e].y;  // conj of the forward result
+        if (addk0) {
+            if constexpr (sizeof(T) == 4) {
+                float s, er;
+                two_sum(p0, add_hi, s, er);
+                p0 = s + (er + add_lo);
+                two_sum(p1, add_hi, s, er);
+                p1 = s + (er + add_lo);
+            } else {
+                p0 = p0 + add_hi;
+                p1 = p1 + add_hi;
+            }
+        }
+        __stcs(o0 + x, p0);
+        __stcs(o1 + x, p1);
+    }
+}
+
+// Standalone Green's-table fill (used when the z pass runs on its own).
+template <typename T>
+__global__ void k_green_params(GreenFill gf) {
+    green_fill<T>(gf, blockIdx.x);
+}
+
+}  // namespace sbp

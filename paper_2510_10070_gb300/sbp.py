@@ -1,0 +1,197 @@
+"""Thin ctypes binding of libsbp.so (argument marshalling only).
+
+Every step of a solve runs in the library's CUDA kernels; PyTorch supplies
+device memory and the current stream.  If the library is missing this module
+raises instead of computing anything on the CPU.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from enum import IntEnum
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsbp.so")
+
+
+class DType(IntEnum):
+    F64 = 0
+    F32 = 1
+    F32_SPLIT_F16 = 2
+    F32_SPLIT_BF16 = 3
+
+
+class Status(IntEnum):
+    OK = 0
+    INVALID_ARG = 1
+    UNSUPPORTED_SIZE = 2
+    OUT_OF_MEMORY = 3
+    CUDA = 4
+    DEVICE_TIMEOUT = 5
+    NOT_SAME_DTYPE = 6
+    UNSUPPORTED_DTYPE = 7
+
+
+class Stage(IntEnum):
+    X_FORWARD = 0
+    Y_FORWARD = 1
+    Z_CONVOLVE = 2
+    Y_INVERSE = 3
+    X_INVERSE = 4
+    GREEN_TABLE = 5
+
+
+class Option(IntEnum):
+    Z_VARIANT = 1
+
+
+class SbpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = Status(status) if status in Status._value2member_map_ else status
+        msg = lib().sbp_status_string(int(status)).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {int(status)})")
+
+
+_c_double = ctypes.c_double
+_c_int = ctypes.c_int
+_vp = ctypes.c_void_p
+
+# name: (restype, argtypes) — the exact set declared in include/sbp.h
+SIGNATURES = {
+    "sbp_plan_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_int, _c_double, _c_double, _c_double,
+                                 _c_double, _c_double, _c_double, _c_int]),
+    "sbp_solve": (_c_int, [_vp, _vp, _vp, _c_double, _vp]),
+    "sbp_solve_batched": (_c_int, [_c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_c_double), _vp]),
+    "sbp_plan_destroy": (None, [_vp]),
+    "sbp_status_string": (ctypes.c_char_p, [_c_int]),
+    "sbp_plan_set_option": (_c_int, [_vp, _c_int, _c_double]),
+    "sbp_plan_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                               ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_size_t)]),
+    "sbp_run_stage": (_c_int, [_vp, _c_int, _vp, _vp, _c_double, _vp]),
+    "sbp_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libsbp.so (built in-tree by ``paper_2510_10070_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2510_10070_gb300.build` "
+                               "(there is no CPU fallback)")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SbpError(status, where)
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """A solver plan for one box (Sect. 2.3 method, see include/sbp.h)."""
+
+    def __init__(self, nx, ny, nz, Lx, Ly, Lz, q=1.5, Omega=1.0, G=1.0, dtype=DType.F64):
+        self._h = ctypes.c_void_p()
+        _check(lib().sbp_plan_create(ctypes.byref(self._h), nx, ny, nz, Lx, Ly, Lz, q, Omega, G, int(dtype)),
+               "sbp_plan_create")
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.Lx, self.Ly, self.Lz, self.q, self.Omega, self.G = Lx, Ly, Lz, q, Omega, G
+        self.dtype = DType(dtype)
+        pitch = ctypes.c_int()
+        ws = ctypes.c_size_t()
+        _check(lib().sbp_plan_info(self._h, None, None, None, None, ctypes.byref(pitch), ctypes.byref(ws)),
+               "sbp_plan_info")
+        self.spectrum_pitch = pitch.value
+        self.workspace_bytes = ws.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        import torch
+
+        return torch.float64 if self.dtype == DType.F64 else torch.float32
+
+    def _check_tensor(self, x, name):
+        import torch
+
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if x.dtype != self.torch_dtype or tuple(x.shape) != (self.nz, self.ny, self.nx) or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {self.torch_dtype} tensor of shape "
+                             f"{(self.nz, self.ny, self.nx)}")
+
+    def solve(self, rho, phi=None, t: float = 0.0, stream=None):
+        """Φ̃ for density ρ̃ at shear time t; returns ``phi`` (allocated if None)."""
+        import torch
+
+        self._check_tensor(rho, "rho")
+        if phi is None:
+            phi = torch.empty_like(rho)
+        self._check_tensor(phi, "phi")
+        _check(lib().sbp_solve(self._h, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                               float(t), _stream_handle(stream)), "sbp_solve")
+        return phi
+
+    def set_option(self, option, value):
+        _check(lib().sbp_plan_set_option(self._h, int(option), float(value)), "sbp_plan_set_option")
+
+    def new_spectrum(self):
+        import torch
+
+        return torch.zeros((self.nz, self.ny, self.spectrum_pitch, 2), dtype=self.torch_dtype, device="cuda")
+
+    def run_stage(self, stage, inp, out, t: float = 0.0, stream=None):
+        ip = ctypes.c_void_p(inp.data_ptr()) if inp is not None else None
+        _check(lib().sbp_run_stage(self._h, int(stage), ip, ctypes.c_void_p(out.data_ptr()), float(t),
+                                   _stream_handle(stream)), f"sbp_run_stage({Stage(stage).name})")
+        return out
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            lib().sbp_plan_destroy(self._h)
+        self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(plans, rhos, phis, ts, stream=None):
+    """Solve box i with plans[i] at time ts[i] (one call, one stream)."""
+    n = len(plans)
+    for p, r, f in zip(plans, rhos, phis):
+        p._check_tensor(r, "rho")
+        p._check_tensor(f, "phi")
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    rp = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in phis])
+    tp = (ctypes.c_double * n)(*[float(t) for t in ts])
+    _check(lib().sbp_solve_batched(n, hp, rp, fp, tp, _stream_handle(stream)), "sbp_solve_batched")
+    return phis
+
+
+def version() -> str:
+    return lib().sbp_version().decode()

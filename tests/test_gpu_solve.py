@@ -1,0 +1,173 @@
+"""End-to-end parity of sbp_solve with the FP64 oracle.
+
+Bars (relative L2): ≤ 1e-12 for SBP_F64 and ≤ 2e-5 for SBP_F32, against the
+oracle on the input exactly as the device holds it.  Small boxes are compared
+element by element; the 256×256×128 box at sampled cells the oracle computes
+one by one; the 512×512×256 box against the FP64 GPU run and, down-sampled to
+64³, against the oracle.
+"""
+
+import numpy as np
+import pytest
+
+import analytic as A
+import oracle as O
+from gpu_helpers import TOL, as_input, rel_l2, to_dev
+from paper_2510_10070_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sbp():
+    from paper_2510_10070_gb300 import sbp as S
+
+    S.lib()
+    return S
+
+
+def _plan(sbp, box, dtype):
+    return sbp.Plan(box.nx, box.ny, box.nz, box.Lx, box.Ly, box.Lz, q=box.q, Omega=box.Omega, G=box.G,
+                    dtype=dtype)
+
+
+def _params(box):
+    return O.SolveParams(box.Lx, box.Ly, box.Lz, q=box.q, Omega=box.Omega, G=box.G)
+
+
+def _gpu_solve(sbp, box, rho, t, dtype):
+    plan = _plan(sbp, box, dtype)
+    phi = plan.solve(to_dev(rho, dtype), t=t)
+    return phi.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_box32_noisy_gaussian(sbp, dtype):
+    box = W.BOX_32
+    rho = W.noisy_gaussian(box, seed=0)
+    got = _gpu_solve(sbp, box, rho, W.T_32, dtype)
+    want = O.solve(as_input(rho, dtype), _params(box), W.T_32)
+    assert rel_l2(got, want) <= TOL[dtype]
+
+
+SHAPES = [(4, 4, 2), (6, 4, 3), (8, 6, 8), (12, 24, 6), (48, 24, 12), (96, 64, 48), (64, 96, 24), (24, 48, 96),
+          (128, 16, 12), (16, 128, 64), (256, 8, 4), (8, 8, 384)]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_random_boxes(sbp, shape, dtype):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 10007 + ny * 101 + nz)
+    box = W.Box(nx, ny, nz, 2.0, 3.0, 1.5, q=1.5, Omega=0.9, G=0.8)
+    rho = rng.standard_normal((nz, ny, nx)) + 0.5
+    for t in (0.0, 0.61, -2.7):
+        got = _gpu_solve(sbp, box, rho, t, dtype)
+        want = O.solve(as_input(rho, dtype), _params(box), t)
+        assert rel_l2(got, want) <= TOL[dtype], (shape, t)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_in_place_and_batched_match_single(sbp, dtype):
+    import torch
+
+    box = W.Box(48, 24, 12, 2.0, 3.0, 1.5)
+    rng = np.random.default_rng(9)
+    rhos = [rng.standard_normal((12, 24, 48)) for _ in range(3)]
+    ts = [0.3, 1.9, -4.0]
+    plans = [_plan(sbp, box, dtype) for _ in range(3)]
+    singles = [plans[i].solve(to_dev(rhos[i], dtype), t=ts[i]) for i in range(3)]
+    dev = [to_dev(r, dtype) for r in rhos]
+    outs = [torch.empty_like(d) for d in dev]
+    sbp.solve_batched(plans, dev, outs, ts)
+    inplace = to_dev(rhos[1], dtype)
+    plans[1].solve(inplace, phi=inplace, t=ts[1])
+    torch.cuda.synchronize()
+    for i in range(3):
+        assert torch.equal(outs[i], singles[i])
+    assert torch.equal(inplace, singles[1])
+
+
+def test_partial_overlap_rejected(sbp):
+    import torch
+
+    box = W.Box(8, 8, 4, 1.0, 1.0, 1.0)
+    plan = _plan(sbp, box, 0)
+    buf = torch.zeros(2 * 8 * 8 * 4, dtype=torch.float64, device="cuda")
+    a = buf[: 8 * 8 * 4].view(4, 8, 8)
+    b = buf[8 * 8 * 2: 8 * 8 * 2 + 8 * 8 * 4].view(4, 8, 8)
+    with pytest.raises(sbp.SbpError):
+        plan.solve(a, phi=b)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_paper_3d_mode_on_gpu(sbp, dtype):
+    # Sect. 3.2 test at 64³: the GPU error against the closed form equals the oracle's.
+    L, H = 6.0, 1.0
+    n = 64
+    box = W.Box(n, n, n, L, L, L)
+    x = A.cell_centres(n, L)
+    k = 2.0 * np.pi / L
+    horiz = np.cos(k * x)[None, :] * np.cos(k * x)[:, None]
+    z = A.cell_centres(n, L)
+    rho = horiz[None] * np.exp(-0.5 * (z / H) ** 2)[:, None, None]
+    got = _gpu_solve(sbp, box, rho, 0.0, dtype)
+    ex = 4.0 * np.pi * horiz[None] * A.mode_profile_paper(z, np.sqrt(2.0) * k, H, L)[:, None, None]
+    err = rel_l2(got, ex)
+    assert 8e-6 < err < 1.1e-5  # 9.35e-6 is the discretisation error of the method at 64³
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_box256_sampled(sbp, dtype):
+    box = W.BOX_256
+    rho = W.lognormal_disc(box, seed=2, sigma=0.5)
+    rng = np.random.default_rng(21)
+    planes = (0, 63, 64, box.nz - 1)
+    pts = [(0, 0, 0), (box.nz - 1, box.ny - 1, box.nx - 1), (64, 17, 255), (63, 128, 128)]
+    pts += [(planes[int(rng.integers(4))], int(rng.integers(box.ny)), int(rng.integers(box.nx))) for _ in range(20)]
+    rho_in = as_input(rho, dtype)
+    plan = _plan(sbp, box, dtype)
+    dev = to_dev(rho, dtype)
+    for t in W.T_256:
+        got_full = plan.solve(dev, t=t).double().cpu().numpy()
+        got = np.array([got_full[i, y, x] for (i, y, x) in pts])
+        want = O.solve_at(rho_in, _params(box), t, pts)
+        assert rel_l2(got, want) <= TOL[dtype], t
+
+
+@pytest.mark.slow
+def test_box256_properties(sbp):
+    import torch
+
+    box = W.BOX_256
+    plan = _plan(sbp, box, 0)
+    rng = np.random.default_rng(5)
+    r1 = to_dev(rng.standard_normal((box.nz, box.ny, box.nx)), 0)
+    r2 = to_dev(W.lognormal_disc(box, seed=2), 0)
+    t = 1.3
+    p1 = plan.solve(r1, t=t)
+    p2 = plan.solve(r2, t=t)
+    lin = plan.solve(2.0 * r1 - 0.5 * r2, t=t)
+    assert rel_l2(lin.cpu().numpy(), (2.0 * p1 - 0.5 * p2).cpu().numpy()) < 1e-12
+    sh = plan.solve(torch.roll(r2, 3, dims=2).contiguous(), t=t)
+    assert rel_l2(sh.cpu().numpy(), torch.roll(p2, 3, dims=2).cpu().numpy()) < 1e-12
+    sh = plan.solve(torch.roll(r2, -5, dims=1).contiguous(), t=t)
+    assert rel_l2(sh.cpu().numpy(), torch.roll(p2, -5, dims=1).cpu().numpy()) < 1e-12
+    period = box.Ly / (box.q * box.Omega * box.Lx)
+    assert rel_l2(plan.solve(r2, t=t + period).cpu().numpy(), p2.cpu().numpy()) < 1e-12
+
+
+@pytest.mark.slow
+def test_box512_fp32_against_fp64_and_oracle_copy(sbp):
+    box = W.BOX_512
+    rho = W.lognormal_disc(box, seed=3, sigma=0.5, dtype=np.float32)
+    f64 = _gpu_solve(sbp, box, rho.astype(np.float64), W.T_512, 0)
+    f32 = _gpu_solve(sbp, box, rho, W.T_512, 1)
+    assert rel_l2(f32, f64) <= TOL[1]
+    # 64³ copy (every 8th x/y, every 4th z sample, same box lengths) vs the oracle
+    small = W.downsample(rho.astype(np.float64), 8, 8, 4)
+    sbox = W.Box(64, 64, 64, box.Lx, box.Ly, box.Lz)
+    want = O.solve(small, _params(sbox), W.T_512)
+    assert rel_l2(_gpu_solve(sbp, sbox, small, W.T_512, 0), want) <= TOL[0]
+    assert rel_l2(_gpu_solve(sbp, sbox, small.astype(np.float32), W.T_512, 1), want) <= TOL[1]

@@ -308,6 +308,11 @@ def test_stage_functions_compose():
     assert np.allclose(O.inverse_horizontal_dft(R), rho, atol=1e-13)
     S = O.plane_sums(rho)
     assert np.allclose(S, R[:, 0, 0].real, atol=1e-12)
+    # half-spectrum inverse = unnormalised library irfft (which also drops
+    # the imaginary parts of the a = 0 and a = nx/2 terms)
+    Xn = X + 1j * rng.standard_normal(X.shape)
+    assert np.allclose(O.inverse_dft_x_half(Xn, 12), np.fft.irfft(Xn, n=12, axis=2) * 12, atol=1e-12)
+    assert np.allclose(O.inverse_dft_x_half(X, 12), rho * 12, atol=1e-12)
 
 
 def test_solve_at_matches_solve():
