@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the shearing-box VGF-HybridBC Poisson solver on GB300.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload batch96|box256|box256_f64]
+                    [--impl ours|reference]
+
+A step is one pass of the whole method over one batch of synthetic input:
+by default the 96-box FP32 batch (32× 64³, 32× 128²×64, 16× 192²×96,
+16× 256²×128, each box with its own shear time and q), solved through
+sbp_solve_batched.  Inputs (931 MB) are larger than L2, so no flush is
+needed between steps.  Under torchrun every rank solves its own copy of the
+batch (weak scaling, no collective on the data path); rank 0 prints one JSON
+line with the whole-job rate.
+
+--impl reference times the FP64 CPU oracle (numpy) on the host cores on a
+bounded sample of the same workload and extrapolates to the batch by the
+oracle's operation count.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s and Gcells/s on 1 GB300 (FP32 & batched vs FP64) at stated rel-L2; % HBM peak"
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_PEAK_FALLBACK}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def build_workload(name):
+    import numpy as np
+
+    from paper_2510_10070_gb300 import workloads as W
+
+    if name == "batch96":
+        case = W.batch_96()
+        boxes, times = case.boxes, [float(t) for t in case.times]
+        rhos = [W.lognormal_disc(b, seed=s, sigma=0.7, dtype=np.float32) for b, s in zip(boxes, case.seeds)]
+        return boxes, rhos, times, 1
+    if name in ("box256", "box256_f64"):
+        box = W.BOX_256
+        rho = W.lognormal_disc(box, seed=2, sigma=0.5)
+        dt = 0 if name == "box256_f64" else 1
+        return [box], [rho if dt == 0 else rho.astype(np.float32)], [1.3], dt
+    raise SystemExit(f"unknown workload {name}")
+
+
+def alg_bytes(box, rb):
+    """B_alg of one solve: read ρ, write φ, and the half spectrum written by
+    the forward passes, read and written by the z pass and read by the
+    inverse passes (three-sweep model)."""
+    N = box.nx * box.ny * box.nz
+    H = (box.nx // 2 + 1) * box.ny * box.nz
+    return 2 * N * rb + 8 * H * rb
+
+
+def z_pass_bytes(box, rb):
+    """Algorithmic bytes of one z-pass launch: read and write the half spectrum."""
+    H = (box.nx // 2 + 1) * box.ny * box.nz
+    return 2 * 2 * H * rb
+
+
+def oracle_cost(box):
+    """Multiply-add count of the oracle's direct sums (for extrapolation)."""
+    nx, ny, nz = box.nx, box.ny, box.nz
+    return (2 * nz * ny * nx * (nx + ny)      # forward + inverse horizontal DFTs
+            + nx * ny * (2 * nz) * (2 * nz - 1)  # vertical kernel by direct sum
+            + nx * ny * nz * nz)              # Toeplitz sums
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+
+def oracle_rate(boxes, rhos, times, budget_s=20.0):
+    """Time the oracle on a bounded sample; return (solves/s, Gcells/s, sample text, cores)."""
+    import numpy as np
+
+    import oracle as O
+
+    order = sorted(range(len(boxes)), key=lambda i: boxes[i].cells)
+    seen, sample = set(), []
+    for i in order:  # one box of each size class, smallest first
+        key = (boxes[i].nx, boxes[i].ny, boxes[i].nz)
+        if key not in seen:
+            seen.add(key)
+            sample.append(i)
+    spent, per_cost = 0.0, []
+    done = []
+    for i in sample:
+        b = boxes[i]
+        est = (spent / sum(oracle_cost(boxes[j]) for j in done) * oracle_cost(b)) if done else 0.0
+        if done and spent + est > budget_s:
+            break
+        p = O.SolveParams(b.Lx, b.Ly, b.Lz, q=b.q, Omega=b.Omega, G=b.G)
+        t0 = time.perf_counter()
+        O.solve(np.asarray(rhos[i], dtype=np.float64), p, times[i])
+        dt = time.perf_counter() - t0
+        spent += dt
+        done.append(i)
+        per_cost.append(dt / oracle_cost(b))
+    sec_per_op = sum(per_cost) / len(per_cost)
+    total = sum(sec_per_op * oracle_cost(b) for b in boxes)
+    cells = sum(b.cells for b in boxes)
+    names = ", ".join(f"{boxes[i].nx}x{boxes[i].ny}x{boxes[i].nz}" for i in done)
+    text = (f"oracle solved one box of each of [{names}] ({spent:.1f} s); the rest of the "
+            f"{len(boxes)}-box workload is extrapolated by the oracle's multiply-add count")
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return len(boxes) / total, cells / total / 1e9, text, cores, total
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="batch96", choices=["batch96", "box256", "box256_f64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        boxes, rhos, times, dt = build_workload(args.workload)
+        vals = []
+        for _ in range(args.warmup + args.steps):
+            r, g, text, cores, tot = oracle_rate(boxes, rhos, times, budget_s=5.0)
+            vals.append(r)
+        v = statistics.median(vals[args.warmup:])
+        gc = v * sum(b.cells for b in boxes) / len(boxes) / 1e9
+        line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * len(boxes) / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload, "boxes": len(boxes), "gcells_per_s": gc},
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": text},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2510_10070_gb300 import sbp
+
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    boxes, rhos_np, times, dt = build_workload(args.workload)
+    tdt = torch.float64 if dt == 0 else torch.float32
+    rb = 8 if dt == 0 else 4
+    plans = [sbp.Plan(b.nx, b.ny, b.nz, b.Lx, b.Ly, b.Lz, q=b.q, Omega=b.Omega, G=b.G, dtype=dt) for b in boxes]
+    rhos = [torch.from_numpy(np.ascontiguousarray(r)).to(device=dev, dtype=tdt) for r in rhos_np]
+    phis = [torch.empty_like(r) for r in rhos]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sbp.solve_batched(plans, rhos, phis, times, stream=stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    nbox = len(boxes)
+    value = world * nbox * args.steps / (ms / 1e3)
+    cells = sum(b.cells for b in boxes)
+    balg = sum(alg_bytes(b, rb) for b in boxes)
+
+    # end to end: pinned host input → device, solve, device → pinned host output
+    host_in = [r.cpu().pin_memory() for r in rhos]
+    host_out = [torch.empty(r.shape, dtype=r.dtype).pin_memory() for r in rhos]
+    h2d = sum(r.numel() * r.element_size() for r in rhos)
+
+    def e2e_step():
+        for hi, d in zip(host_in, rhos):
+            d.copy_(hi, non_blocking=True)
+        step()
+        for ho, d in zip(host_out, phis):
+            ho.copy_(d, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    e2e_steps = max(3, args.steps // 4)
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2.record(stream)
+    barrier()
+    e2e_value = world * nbox * e2e_steps / (s2.elapsed_time(e2) / 1e3)
+
+    # dominant kernel: the z pass of the largest box, timed alone with CUDA
+    # events on the launching stream, on the same data
+    big = max(range(nbox), key=lambda i: boxes[i].cells)
+    bp = plans[big]
+    spec = bp.new_spectrum()
+    bp.run_stage(sbp.Stage.X_FORWARD, rhos[big], spec, stream=stream)
+    bp.run_stage(sbp.Stage.Y_FORWARD, spec, spec, stream=stream)
+    bp.run_stage(sbp.Stage.GREEN_FILL, None, spec, t=times[big], stream=stream)
+    zreps = 20
+    for _ in range(3):
+        bp.run_stage(sbp.Stage.Z_CONVOLVE, spec, spec, stream=stream)
+    zs, ze = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    zs.record(stream)
+    for _ in range(zreps):
+        bp.run_stage(sbp.Stage.Z_CONVOLVE, spec, spec, stream=stream)
+    ze.record(stream)
+    torch.cuda.synchronize()
+    z_ms = zs.elapsed_time(ze) / zreps
+    peaks, peak_src = measured_peaks()
+    zbytes = z_pass_bytes(boxes[big], rb)
+    z_gbs = zbytes / (z_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_z_padded/k_z_pass, {boxes[big].nx}x{boxes[big].ny}x{boxes[big].nz}",
+                "achieved": z_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": z_gbs / peaks["hbm_gbs"],
+                "traffic": None, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "step_alg_gbs": balg / (ms_per_step / 1e3) / 1e9,
+                "step_frac": balg / (ms_per_step / 1e3) / 1e9 / peaks["hbm_gbs"]}
+
+    # FP64 and FP32 single-box reference numbers (the "vs FP64" of the metric)
+    side = {}
+    if args.workload == "batch96":
+        from paper_2510_10070_gb300 import workloads as W
+
+        rho256 = W.lognormal_disc(W.BOX_256, seed=2, sigma=0.5)
+        for name, d in (("box256_fp64", 0), ("box256_fp32", 1)):
+            b = W.BOX_256
+            p = sbp.Plan(b.nx, b.ny, b.nz, b.Lx, b.Ly, b.Lz, q=b.q, dtype=d)
+            r = torch.from_numpy(rho256).to(device=dev, dtype=torch.float64 if d == 0 else torch.float32)
+            f = torch.empty_like(r)
+            for _ in range(3):
+                p.solve(r, f, t=1.3, stream=stream)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5 if d == 0 else 20
+            a0.record(stream)
+            for _ in range(reps):
+                p.solve(r, f, t=1.3, stream=stream)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t_ms = a0.elapsed_time(a1) / reps
+            side[name] = {"ms_per_solve": t_ms, "solves_per_s": 1e3 / t_ms,
+                          "gcells_per_s": b.cells / (t_ms / 1e3) / 1e9}
+        side["batch_fp32_vs_box256_fp64_cells_speedup"] = (cells / (ms_per_step / 1e3) / 1e9) / \
+            side["box256_fp64"]["gcells_per_s"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, g, text, cores, tot = oracle_rate(boxes, rhos_np, times)
+        cpu = {"value": r, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": text}
+
+    per_box_kernels = 5
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if dt == 0 else "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "boxes": nbox, "cells_per_step": cells,
+                       "gcells_per_s": world * cells * args.steps / (ms / 1e3) / 1e9,
+                       "alg_bytes_per_step": balg, "l2": "inputs larger than L2 (no flush needed)"
+                       if sum(r.numel() * r.element_size() for r in rhos) > 129e6 else "inputs smaller than L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+            "gpu_launches": per_box_kernels * nbox * args.steps,
+            "clocks": clk.summary(),
+            "single_box": side,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

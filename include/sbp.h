@@ -69,7 +69,8 @@ typedef enum {
     SBP_STAGE_Z_CONVOLVE = 2,
     SBP_STAGE_Y_INVERSE = 3,
     SBP_STAGE_X_INVERSE = 4,
-    SBP_STAGE_GREEN_TABLE = 5
+    SBP_STAGE_GREEN_TABLE = 5,
+    SBP_STAGE_GREEN_FILL = 6
 } sbp_stage;
 
 /*
@@ -151,11 +152,16 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  *                         X[z][y][a] = Σ_x ρ e^{-2πi a x/nx}, a ≤ nx/2.
  *   SBP_STAGE_Y_FORWARD : in = out = spectrum (in place, in must equal out);
  *                         DFT over y with e^{-2πi b y/ny}.
+ *   SBP_STAGE_GREEN_FILL: in ignored, out = the spectrum buffer (unused);
+ *                         fills the plan's internal Green's table for time t
+ *                         (FP64 arithmetic), as the x forward pass of a solve
+ *                         does.
  *   SBP_STAGE_Z_CONVOLVE: in = out = spectrum; for each column (b, a) the
  *                         padded vertical convolution with the Green's kernel
- *                         at shear time t, scaled by 4πG/(nx·ny·2nz).  For
- *                         SBP_F32 the (0,0) column is left to the FP64 mean
- *                         mode and written as zero.
+ *                         of the plan's internal table (the time of the last
+ *                         GREEN_FILL or solve), scaled by 4πG/(nx·ny·2nz).
+ *                         For SBP_F32 the (0,0) column is left to the FP64
+ *                         mean mode and written as zero.
  *   SBP_STAGE_Y_INVERSE : in = out = spectrum; DFT over y with e^{+2πi b y/ny}.
  *   SBP_STAGE_X_INVERSE : in = spectrum, out = real [nz][ny][nx]; the
  *                         half-spectrum inverse x DFT (real part, unscaled).

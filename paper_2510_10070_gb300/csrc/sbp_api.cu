@@ -451,11 +451,12 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
             ky.y_fwd<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
                                                                    make_yargs<T>(p));
             break;
+        case SBP_STAGE_GREEN_FILL: {
+            const int blocks = (p->h * p->ny + 255) / 256;
+            k_green_params<T><<<blocks, 256, 0, st>>>(make_green_fill(p, t, blocks));
+            break;
+        }
         case SBP_STAGE_Z_CONVOLVE:
-            if (!fused) {
-                const int blocks = (p->h * p->ny + 255) / 256;
-                k_green_params<T><<<blocks, 256, 0, st>>>(make_green_fill(p, t, blocks));
-            }
             reinterpret_cast<ZKernel<T>>(p->z_fn)<<<p->zp.grid, p->zp.threads, p->zp.smem, st>>>(
                 W, static_cast<const cpx<T>*>(p->tw_z),
                 static_cast<const cpx<T>*>(p->z_padded ? p->tw_M : p->tw_2z),
@@ -651,8 +652,8 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int*
 
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream) {
     if (!p || !out || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
-    if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_TABLE) return SBP_ERR_INVALID_ARG;
-    if (stage != SBP_STAGE_GREEN_TABLE && !in) return SBP_ERR_INVALID_ARG;
+    if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_FILL) return SBP_ERR_INVALID_ARG;
+    if (stage != SBP_STAGE_GREEN_TABLE && stage != SBP_STAGE_GREEN_FILL && !in) return SBP_ERR_INVALID_ARG;
     if ((stage == SBP_STAGE_Y_FORWARD || stage == SBP_STAGE_Z_CONVOLVE || stage == SBP_STAGE_Y_INVERSE) &&
         in != out)
         return SBP_ERR_INVALID_ARG;

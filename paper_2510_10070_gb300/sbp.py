@@ -40,6 +40,7 @@ class Stage(IntEnum):
     Y_INVERSE = 3
     X_INVERSE = 4
     GREEN_TABLE = 5
+    GREEN_FILL = 6
 
 
 class Option(IntEnum):

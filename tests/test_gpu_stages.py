@@ -76,6 +76,7 @@ def test_z_convolve(sbp, shape, dtype, t):
     rng = np.random.default_rng(3)
     X = rng.standard_normal((nz, ny, h)) + 1j * rng.standard_normal((nz, ny, h))
     spec = np_to_spec(X, plan.spectrum_pitch, dtype)
+    plan.run_stage(sbp.Stage.GREEN_FILL, None, spec, t=t)
     plan.run_stage(sbp.Stage.Z_CONVOLVE, spec, spec, t=t)
     p = O.SolveParams(*L, q=1.5, Omega=1.0, G=G)
     c = O.vertical_kernel(O.green_eff(nx, ny, nz, p, t)[:, :h], nz)
@@ -100,6 +101,7 @@ def test_z_convolve_variants(sbp, shape, variant):
     rng = np.random.default_rng(13)
     X = rng.standard_normal((nz, ny, h)) + 1j * rng.standard_normal((nz, ny, h))
     spec = np_to_spec(X, plan.spectrum_pitch, 1)
+    plan.run_stage(sbp.Stage.GREEN_FILL, None, spec, t=0.9)
     plan.run_stage(sbp.Stage.Z_CONVOLVE, spec, spec, t=0.9)
     p = O.SolveParams(*L, q=1.5, Omega=1.0, G=0.7)
     c = O.vertical_kernel(O.green_eff(nx, ny, nz, p, 0.9)[:, :h], nz)
