@@ -59,7 +59,8 @@ typedef enum {
     SBP_ERR_CUDA = 4,              /* a CUDA runtime call or kernel launch failed */
     SBP_ERR_DEVICE_TIMEOUT = 5,    /* a bounded device-side wait gave up */
     SBP_ERR_NOT_SAME_DTYPE = 6,    /* batched call mixing dtypes */
-    SBP_ERR_UNSUPPORTED_DTYPE = 7  /* dtype not built in this library */
+    SBP_ERR_UNSUPPORTED_DTYPE = 7, /* dtype not built in this library */
+    SBP_ERR_SCRATCH_LIMIT = 8      /* box too large for sbp_solve_noalloc's fixed workspace */
 } sbp_status;
 
 /* Plan stages that sbp_run_stage can run alone (see there). */
@@ -171,6 +172,36 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  * The FP32 mean-mode side path is not part of any single stage.
  */
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream);
+
+/*
+ * sbp_solve_noalloc — an FP32 solve that allocates no device memory.
+ *
+ * The paper has no counterpart: this call exists for host programs that may
+ * not allocate device memory while they run (codes that give all device
+ * memory to their own pool at start-up, real-time loops that cannot take the
+ * device synchronisation an allocation implies, plugin hosts that only hand a
+ * library their own buffers).  It computes what sbp_plan_create +
+ * sbp_solve(dtype SBP_F32) compute, from the same arguments, with the
+ * workspace in one fixed 40 MiB array of device global memory that the
+ * library declares statically: every GPU that loads the library holds that
+ * array until the process exits.
+ *
+ * rho, phi: device float arrays [nz][ny][nx], 16-byte aligned, phi == rho
+ * allowed, no other overlap.  The sizes, box lengths and parameters follow
+ * sbp_plan_create.  A box whose workspace does not fit the 40 MiB (about
+ * 256×256×128 cells is the largest cube-like box that does) returns
+ * SBP_ERR_SCRATCH_LIMIT before touching the device.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any CUDA
+ * stream capture.  Every call on a device shares the array, which keeps the
+ * last call's contents (every byte a call reads is written earlier in the
+ * same call, so nothing needs clearing).  Calls whose work overlaps on the
+ * GPU, for example on two streams, race on the array: order them.
+ */
+sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                             double q, double Omega, double G,
+                             const float* rho, float* phi, double t, void* stream);
 
 /* sbp_version — library version string. */
 const char* sbp_version(void);

@@ -621,6 +621,7 @@ const char* sbp_status_string(sbp_status s) {
         case SBP_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
         case SBP_ERR_NOT_SAME_DTYPE: return "batched plans differ in dtype";
         case SBP_ERR_UNSUPPORTED_DTYPE: return "dtype not built in this library";
+        case SBP_ERR_SCRATCH_LIMIT: return "box exceeds the 40 MiB fixed workspace of sbp_solve_noalloc";
     }
     return "unknown status";
 }

@@ -31,6 +31,7 @@ class Status(IntEnum):
     DEVICE_TIMEOUT = 5
     NOT_SAME_DTYPE = 6
     UNSUPPORTED_DTYPE = 7
+    SCRATCH_LIMIT = 8
 
 
 class Stage(IntEnum):
@@ -72,6 +73,8 @@ SIGNATURES = {
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_size_t)]),
     "sbp_run_stage": (_c_int, [_vp, _c_int, _vp, _vp, _c_double, _vp]),
     "sbp_version": (ctypes.c_char_p, []),
+    "sbp_solve_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
+                                   _c_double, _vp, _vp, _c_double, _vp]),
 }
 
 _lib = None
@@ -192,6 +195,27 @@ def solve_batched(plans, rhos, phis, ts, stream=None):
     tp = (ctypes.c_double * n)(*[float(t) for t in ts])
     _check(lib().sbp_solve_batched(n, hp, rp, fp, tp, _stream_handle(stream)), "sbp_solve_batched")
     return phis
+
+
+def solve_noalloc(rho, phi, Lx, Ly, Lz, q=1.5, Omega=1.0, G=1.0, t=0.0, stream=None):
+    """FP32 solve without any device allocation (fixed 40 MiB library workspace).
+
+    For programs that may not allocate device memory while they run; see
+    sbp_solve_noalloc in include/sbp.h.  ``rho`` and ``phi`` are contiguous
+    float32 CUDA tensors [nz, ny, nx]; the caller allocates them.
+    """
+    import torch
+
+    for x, name in ((rho, "rho"), (phi, "phi")):
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if rho.dim() != 3 or tuple(phi.shape) != tuple(rho.shape):
+        raise ValueError("rho and phi must have the same shape [nz, ny, nx]")
+    nz, ny, nx = rho.shape
+    _check(lib().sbp_solve_noalloc(nx, ny, nz, Lx, Ly, Lz, q, Omega, G, ctypes.c_void_p(rho.data_ptr()),
+                                   ctypes.c_void_p(phi.data_ptr()), float(t), _stream_handle(stream)),
+           "sbp_solve_noalloc")
+    return phi
 
 
 def version() -> str:

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings(lib):
-    for s in range(8):
+    for s in range(9):
         assert lib.sbp_status_string(s)
     assert lib.sbp_status_string(0) == b"ok"
     assert lib.sbp_version().startswith(b"sbp")
