@@ -106,10 +106,18 @@ sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* str
 /*
  * sbp_solve_batched — nbox independent solves on one stream.
  *
- * Each box i is solved exactly as sbp_solve(plans[i], rho[i], phi[i], t[i]).
- * All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE) and the device.
- * A plan may appear only once per call.  plans, rho, phi and t are HOST arrays
- * of length nbox; rho[i] and phi[i] are device pointers.
+ * Each box i is solved exactly as sbp_solve(plans[i], rho[i], phi[i], t[i])
+ * (bit for bit).  All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE)
+ * and the device.  A plan may appear only once per call.  plans, rho, phi and
+ * t are HOST arrays of length nbox; rho[i] and phi[i] are device pointers.
+ *
+ * Execution: the boxes' pass kernels are captured once into a CUDA graph with
+ * K parallel branches and cached by the exact (plans, rho, phi) tuple; a call
+ * with a cached tuple copies the nbox shear parameters to the device and
+ * replays the graph on `stream`.  The first call of a tuple chooses K by
+ * timing candidate graphs on `stream` (it synchronises that stream once);
+ * the environment variable SBP_BATCH_BRANCHES=K forces K.  Destroying any
+ * plan of a tuple drops its cached graph.
  */
 sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const* rho,
                              void* const* phi, const double* t, void* stream);

@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <cstdlib>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -120,9 +122,8 @@ size_t zpass_smem(int n, int C) {
 template <typename T>
 size_t zpad_smem(int n, int C) {
     const size_t cs = sizeof(cpx<T>);
-    const size_t kz2_bytes = align_up((size_t)(n + 1) * sizeof(T), 16);
     const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
-    return 2 * (size_t)n * cs + kz2_bytes + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
+    return 2 * (size_t)n * cs + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
 }
 
 template <typename T>
@@ -169,8 +170,12 @@ bool configure_z(sbp_plan_s* p, int variant) {
     const int per_col = (padded || joint ? 1 : 2) * P.Tf;
     auto smem = [&](int C) { return padded ? zpad_smem<T>(p->nz, C) : zpass_smem<T>(p->nz, C); };
     int C = std::max(1, std::min(cmax, kMaxThreads / per_col));
-    C = std::min(C, p->h);
-    while (C > 1 && smem(C) > kSmemBudget) --C;
+    if (padded) {
+        C = zpad_cols(p->nz, E, f64);  // compiled into the kernel
+    } else {
+        C = std::min(C, p->h);
+        while (C > 1 && smem(C) > kSmemBudget) --C;
+    }
     if (C * per_col > kMaxThreads || smem(C) > kSmemBudget) return false;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
         cudaGetLastError();
@@ -211,8 +216,12 @@ bool configure(sbp_plan_s* p) {
     {
         const int Tf = p->py.Tf;
         int C = std::max(1, std::min(cmax, kMaxThreads / Tf));
-        C = std::min(C, p->h);
-        while (C > 1 && ypass_smem<T>(p->ny, C) > kSmemBudget) --C;
+        if (is_static_len<T>(p->ny)) {
+            C = ypass_cols(p->ny, f64);  // compiled into the static kernel
+        } else {
+            C = std::min(C, p->h);
+            while (C > 1 && ypass_smem<T>(p->ny, C) > kSmemBudget) --C;
+        }
         p->yp.E = p->py.E;
         p->yp.C = C;
         p->yp.threads = C * Tf;
@@ -377,6 +386,7 @@ GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
     g.Ly = p->Ly;
     g.L = p->Lz;
     g.s = shear_s(p, t);
+    g.s_dev = nullptr;
     return g;
 }
 
@@ -411,6 +421,7 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     a.ny = p->ny;
     a.C = p->zp.C;
     a.L = p->Lz;
+    a.kzc = (M_PI / p->Lz) * (M_PI / p->Lz);
     a.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * 2.0 * p->nz);
     const bool f32 = !f64_of(p);
     a.zero_k0 = f32 ? 1 : 0;
@@ -429,7 +440,7 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
 // only its own transform; the z pass then fills its table first.
 template <typename T>
 sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, double t, cudaStream_t st,
-                        bool fused) {
+                        bool fused, const double* s_dev = nullptr) {
     const KernelSet<T> kx = kernels_for<T>(p->nx, p->px.E), ky = kernels_for<T>(p->ny, p->py.E);
     const bool f32 = !f64_of(p);
     cpx<T>* W = static_cast<cpx<T>*>(out);
@@ -440,6 +451,7 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
             if (fused) {
                 a.green_blocks = p->green_blocks;
                 a.gf = make_green_fill(p, t, p->green_blocks);
+                a.gf.s_dev = s_dev;
                 grid.x += p->green_blocks;
             }
             double* sums = (f32 && fused) ? p->tile_sums : nullptr;
@@ -486,9 +498,10 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
 }
 
 template <typename T>
-sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st) {
+sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
+                   const double* s_dev = nullptr) {
     sbp_status s;
-    if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true)) != SBP_OK) return s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true, s_dev)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Y_FORWARD, p->W, p->W, t, st, true)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Z_CONVOLVE, p->W, p->W, t, st, true)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Y_INVERSE, p->W, p->W, t, st, true)) != SBP_OK) return s;
@@ -505,6 +518,155 @@ sbp_status check_io(const sbp_plan_s* p, const void* rho, const void* phi, doubl
     const size_t bytes = (size_t)p->nx * p->ny * p->nz * p->rsize;
     const uintptr_t r0 = reinterpret_cast<uintptr_t>(rho), f0 = reinterpret_cast<uintptr_t>(phi);
     if (r0 != f0 && r0 < f0 + bytes && f0 < r0 + bytes) return SBP_ERR_INVALID_ARG;
+    return SBP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched executor: the boxes' pass kernels captured once into a CUDA graph
+// with K parallel branches (boxes spread over the branches, largest first),
+// cached by the exact (plans, rho, phi) tuple.  Per call only the shear
+// parameters change: one async copy refreshes a device table that the
+// x-forward Green's blocks read, then the graph is replayed.  K is chosen on
+// the first call by timing the candidates (SBP_BATCH_BRANCHES forces it).
+// ---------------------------------------------------------------------------
+struct BatchExec {
+    std::vector<sbp_plan_s*> plans;
+    std::vector<const void*> rho;
+    std::vector<void*> phi;
+    int device = 0;
+    double* s_dev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int branches = 0;
+    float tuned_ms = 0.f;
+};
+
+std::mutex g_exec_mu;
+std::vector<BatchExec*> g_execs;
+
+void free_exec(BatchExec* e) {
+    if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->s_dev) cudaFree(e->s_dev);
+    delete e;
+}
+
+sbp_status capture_batch(BatchExec* e, int K, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
+    const int n = (int)e->plans.size();
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> br(K, nullptr);
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(K, nullptr);
+    sbp_status st = SBP_OK;
+    bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < K; ++k)
+        ok = cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) == cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        cudaEventRecord(fork, cap);
+        for (int k = 0; k < K; ++k) cudaStreamWaitEvent(br[k], fork, 0);
+        // largest boxes first, each to the least loaded branch
+        std::vector<int> order(n);
+        for (int i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const sbp_plan_s* pa = e->plans[a];
+            const sbp_plan_s* pb = e->plans[b];
+            return (size_t)pa->nx * pa->ny * pa->nz > (size_t)pb->nx * pb->ny * pb->nz;
+        });
+        std::vector<double> load(K, 0.0);
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            sbp_plan_s* p = e->plans[i];
+            load[k] += (double)p->nx * p->ny * p->nz;
+            const sbp_status s = f64_of(p) ? solve_t<double>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i)
+                                           : solve_t<float>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i);
+            if (s != SBP_OK && st == SBP_OK) st = s;
+        }
+        for (int k = 0; k < K; ++k) {
+            cudaEventRecord(join[k], br[k]);
+            cudaStreamWaitEvent(cap, join[k], 0);
+        }
+        if (cudaStreamEndCapture(cap, &graph) != cudaSuccess) ok = false;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (ok && st == SBP_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) ok = false;
+    for (int k = 0; k < K; ++k) {
+        if (br[k]) cudaStreamDestroy(br[k]);
+        if (join[k]) cudaEventDestroy(join[k]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (cap) cudaStreamDestroy(cap);
+    if (!ok || st != SBP_OK) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != SBP_OK ? st : SBP_ERR_CUDA;
+    }
+    *graph_out = graph;
+    *exec_out = exec;
+    return SBP_OK;
+}
+
+// Build the executor's graph, choosing K by timing when not forced.
+sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
+    const int n = (int)e->plans.size();
+    std::vector<int> cands;
+    if (const char* env = std::getenv("SBP_BATCH_BRANCHES")) {
+        const int k = std::atoi(env);
+        if (k >= 1) cands.push_back(std::min(k, std::max(1, n)));
+    }
+    if (cands.empty())
+        for (int k : {1, 2, 4, 8, 16, 32})
+            if (k <= std::max(1, n)) cands.push_back(k);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cands.size() > 1 && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    float best = 0.f;
+    for (int K : cands) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        const sbp_status s = capture_batch(e, K, &g, &x);
+        if (s != SBP_OK) {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+            return s;
+        }
+        float ms = 0.f;
+        if (cands.size() > 1) {
+            cudaGraphLaunch(x, st);
+            cudaEventRecord(a, st);
+            for (int r = 0; r < 3; ++r) cudaGraphLaunch(x, st);
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+                cudaGraphExecDestroy(x);
+                cudaGraphDestroy(g);
+                cudaEventDestroy(a);
+                cudaEventDestroy(b);
+                cudaGetLastError();
+                return SBP_ERR_CUDA;
+            }
+        }
+        if (!e->exec || ms < best) {
+            if (e->exec) cudaGraphExecDestroy(e->exec);
+            if (e->graph) cudaGraphDestroy(e->graph);
+            e->exec = x;
+            e->graph = g;
+            e->branches = K;
+            best = ms;
+        } else {
+            cudaGraphExecDestroy(x);
+            cudaGraphDestroy(g);
+        }
+    }
+    e->tuned_ms = best / 3.f;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
     return SBP_OK;
 }
 
@@ -594,9 +756,56 @@ sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const*
         const sbp_status v = check_io(plans[i], rho[i], phi[i], t[i]);
         if (v != SBP_OK) return v;
     }
-    for (int i = 0; i < nbox; ++i) {
-        const sbp_status s = sbp_solve(plans[i], rho[i], phi[i], t[i], stream);
-        if (s != SBP_OK) return s;
+    if (nbox == 0) return SBP_OK;
+    DeviceGuard g(plans[0]->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    BatchExec* e = nullptr;
+    for (BatchExec* c : g_execs) {
+        if ((int)c->plans.size() != nbox) continue;
+        bool same = true;
+        for (int i = 0; same && i < nbox; ++i)
+            same = c->plans[i] == plans[i] && c->rho[i] == rho[i] && c->phi[i] == phi[i];
+        if (same) {
+            e = c;
+            break;
+        }
+    }
+    std::vector<double> s_host(nbox);
+    for (int i = 0; i < nbox; ++i) s_host[i] = shear_s(plans[i], t[i]);
+    const bool fresh = (e == nullptr);
+    if (fresh) {
+        e = new (std::nothrow) BatchExec();
+        if (!e) return SBP_ERR_OUT_OF_MEMORY;
+        e->plans.assign(plans, plans + nbox);
+        e->rho.assign(rho, rho + nbox);
+        e->phi.assign(phi, phi + nbox);
+        e->device = plans[0]->device;
+        if (cudaMalloc(&e->s_dev, sizeof(double) * nbox) != cudaSuccess) {
+            cudaGetLastError();
+            e->s_dev = nullptr;
+            free_exec(e);
+            return SBP_ERR_OUT_OF_MEMORY;
+        }
+    }
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    if (cudaMemcpyAsync(e->s_dev, s_host.data(), sizeof(double) * nbox, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (fresh) free_exec(e);
+        return SBP_ERR_CUDA;
+    }
+    if (fresh) {
+        const sbp_status s = tune_batch(e, st);
+        if (s != SBP_OK) {
+            free_exec(e);
+            return s;
+        }
+        g_execs.push_back(e);
+    }
+    if (cudaGraphLaunch(e->exec, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
     }
     return SBP_OK;
 }
@@ -607,6 +816,19 @@ void sbp_plan_destroy(sbp_plan p) {
         DeviceGuard g(p->device);
         cudaDeviceSynchronize();
         cudaGetLastError();
+        {
+            // batched executors that reference this plan go with it
+            std::lock_guard<std::mutex> lock(g_exec_mu);
+            for (size_t i = 0; i < g_execs.size();) {
+                BatchExec* e = g_execs[i];
+                if (std::find(e->plans.begin(), e->plans.end(), p) != e->plans.end()) {
+                    free_exec(e);
+                    g_execs.erase(g_execs.begin() + i);
+                } else {
+                    ++i;
+                }
+            }
+        }
         free_plan(p);
     }
 }

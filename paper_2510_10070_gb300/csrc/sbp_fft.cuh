@@ -305,28 +305,37 @@ struct FftPlan {
     int tws[kMaxStages];  // n / (ns·radix): table stride of the stage twiddle
 };
 
-// Shared-memory view of one transform's exchange buffer.  Column layout
-// (stride > 0): element i at base[i * stride], for tiles whose lanes run
-// across columns.  Row layout (stride == 0): element i at base[i + i/16],
-// one pad slot per 16 elements, for tiles whose lanes run along the row.
-template <typename T>
+// Shared-memory views of one transform's exchange buffer.
+//   S > 0  : column layout with compile-time stride S (element i at base[i·S]);
+//   S == 0 : row layout, one pad slot per 16 elements (base[i + i/16]);
+//   S < 0  : column layout with the runtime stride `stride`.
+// Column layouts serve tiles whose lanes run across columns, the row layout
+// tiles whose lanes run along the row.
+template <typename T, int S = -1>
 struct SmemCol {
     cpx<T>* base;
     int stride;
     __device__ __forceinline__ cpx<T>& operator[](int i) const {
-        return stride > 0 ? base[i * stride] : base[i + (i >> 4)];
+        if constexpr (S > 0) {
+            return base[i * S];
+        } else if constexpr (S == 0) {
+            return base[i + (i >> 4)];
+        } else {
+            return base[i * stride];
+        }
     }
 };
+template <typename T>
+using SmemRow = SmemCol<T, 0>;
 // Complex slots of one row-layout buffer of n elements.
 __host__ __device__ constexpr int padded_row(int n) { return n + (n >> 4) + 1; }
 
 // One radix-R stage on the E register values of thread t.  If `last`, the
 // outputs stay in registers (they land in the thread's own index set);
 // otherwise they are written to the exchange buffer.
-template <int R, int E, int NCOL, typename T>
+template <int R, int E, int NCOL, typename T, typename BUF>
 __device__ __forceinline__ void stage_radix(cpx<T> (&v)[NCOL][E], int t, int Tf, int Ns, int tws,
-                                            const cpx<T>* __restrict__ tw, const SmemCol<T> (&buf)[NCOL],
-                                            bool last) {
+                                            const cpx<T>* __restrict__ tw, const BUF (&buf)[NCOL], bool last) {
     constexpr int B = E / R;  // butterflies per thread
 #pragma unroll
     for (int u = 0; u < B; ++u) {
@@ -358,9 +367,9 @@ __device__ __forceinline__ void stage_radix(cpx<T> (&v)[NCOL][E], int t, int Tf,
 // Caller contract: every thread of the block calls this the same number of
 // times (it contains __syncthreads), `tw` is the length-n table
 // tw[k] = e^{-2πi k/n}, and the exchange buffers are not in use by anyone.
-template <int E, int NCOL, typename T>
+template <int E, int NCOL, typename T, typename BUF>
 __device__ __forceinline__ void fft_forward(cpx<T> (&v)[NCOL][E], int t, const FftPlan& P,
-                                            const cpx<T>* __restrict__ tw, const SmemCol<T> (&buf)[NCOL]) {
+                                            const cpx<T>* __restrict__ tw, const BUF (&buf)[NCOL]) {
     const int Tf = P.Tf;
     for (int s = 0; s < P.nstage; ++s) {
         const bool last = (s + 1 == P.nstage);
@@ -368,28 +377,28 @@ __device__ __forceinline__ void fft_forward(cpx<T> (&v)[NCOL][E], int t, const F
         if (!last) __syncthreads();  // previous readers of the buffer are done
         switch (R) {
             case 2:
-                if constexpr (E % 2 == 0) stage_radix<2, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 2 == 0) stage_radix<2, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 3:
-                if constexpr (E % 3 == 0) stage_radix<3, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 3 == 0) stage_radix<3, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 4:
-                if constexpr (E % 4 == 0) stage_radix<4, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 4 == 0) stage_radix<4, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 6:
-                if constexpr (E % 6 == 0) stage_radix<6, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 6 == 0) stage_radix<6, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 8:
-                if constexpr (E % 8 == 0) stage_radix<8, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 8 == 0) stage_radix<8, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 12:
-                if constexpr (E % 12 == 0) stage_radix<12, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 12 == 0) stage_radix<12, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 16:
-                if constexpr (E % 16 == 0) stage_radix<16, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 16 == 0) stage_radix<16, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             case 24:
-                if constexpr (E % 24 == 0) stage_radix<24, E, NCOL, T>(v, t, Tf, Ns, tws, tw, buf, last);
+                if constexpr (E % 24 == 0) stage_radix<24, E, NCOL, T, BUF>(v, t, Tf, Ns, tws, tw, buf, last);
                 break;
             default:
                 break;
@@ -459,9 +468,9 @@ __host__ __device__ constexpr int static_ns(int n, int E, int stage) {
 }
 
 // One radix-R stage with every size known at compile time.
-template <int R, int E, int NCOL, int Ns, int TWS, int TF, bool LAST, typename T>
+template <int R, int E, int NCOL, int Ns, int TWS, int TF, bool LAST, typename T, typename BUF>
 __device__ __forceinline__ void stage_static(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ tw,
-                                             const SmemCol<T> (&buf)[NCOL]) {
+                                             const BUF (&buf)[NCOL]) {
     constexpr int B = E / R;
 #pragma unroll
     for (int u = 0; u < B; ++u) {
@@ -494,9 +503,9 @@ __device__ __forceinline__ void stage_static(cpx<T> (&v)[NCOL][E], int t, const 
     }
 }
 
-template <int N, int E, int S, int NCOL, typename T>
+template <int N, int E, int S, int NCOL, typename T, typename BUF>
 __device__ __forceinline__ void fft_static(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ tw,
-                                           const SmemCol<T> (&buf)[NCOL]) {
+                                           const BUF (&buf)[NCOL]) {
     constexpr int NST = static_nstage(N, E);
     static_assert(NST > 0 && NST <= kMaxStages, "length not supported by the radix set");
     if constexpr (S < NST) {
@@ -506,7 +515,7 @@ __device__ __forceinline__ void fft_static(cpx<T> (&v)[NCOL][E], int t, const cp
         constexpr int TF = N / E;
         constexpr bool LAST = (S + 1 == NST);
         if constexpr (!LAST) __syncthreads();
-        stage_static<R, E, NCOL, Ns, TWS, TF, LAST, T>(v, t, tw, buf);
+        stage_static<R, E, NCOL, Ns, TWS, TF, LAST, T, BUF>(v, t, tw, buf);
         if constexpr (!LAST) {
             __syncthreads();
 #pragma unroll
@@ -515,7 +524,7 @@ __device__ __forceinline__ void fft_static(cpx<T> (&v)[NCOL][E], int t, const cp
                 for (int e = 0; e < E; ++e) v[c][e] = buf[c][t + TF * e];
             }
         }
-        fft_static<N, E, S + 1, NCOL, T>(v, t, tw, buf);
+        fft_static<N, E, S + 1, NCOL, T, BUF>(v, t, tw, buf);
     }
 }
 
@@ -523,9 +532,9 @@ __device__ __forceinline__ void fft_static(cpx<T> (&v)[NCOL][E], int t, const cp
 // v[e] = x[t + Tf·e] with v[e] = 0 for e ≥ E/2 (never read).  The first
 // stage must have radix E (one butterfly per thread) so that exactly its
 // upper inputs vanish.
-template <int M, int E, int NCOL, typename T>
+template <int M, int E, int NCOL, typename T, typename BUF>
 __device__ __forceinline__ void fft_static_padded(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ tw,
-                                                  const SmemCol<T> (&buf)[NCOL]) {
+                                                  const BUF (&buf)[NCOL]) {
     constexpr int NST = static_nstage(M, E);
     static_assert(static_radix(M, E, 0) == E, "padded first stage needs one butterfly per thread");
     static_assert(NST >= 2, "padded transform needs at least two stages");
@@ -546,17 +555,17 @@ __device__ __forceinline__ void fft_static_padded(cpx<T> (&v)[NCOL][E], int t, c
 #pragma unroll
         for (int e = 0; e < E; ++e) v[c][e] = buf[c][t + TF * e];
     }
-    fft_static<M, E, 1, NCOL, T>(v, t, tw, buf);
+    fft_static<M, E, 1, NCOL, T, BUF>(v, t, tw, buf);
 }
 
 // Forward transform: compile-time plan when NS > 0, else the runtime plan P.
-template <int NS, int E, int NCOL, typename T>
+template <int NS, int E, int NCOL, typename T, typename BUF>
 __device__ __forceinline__ void fft_run(cpx<T> (&v)[NCOL][E], int t, const FftPlan& P, const cpx<T>* __restrict__ tw,
-                                        const SmemCol<T> (&buf)[NCOL]) {
+                                        const BUF (&buf)[NCOL]) {
     if constexpr (NS > 0) {
-        fft_static<NS, E, 0, NCOL, T>(v, t, tw, buf);
+        fft_static<NS, E, 0, NCOL, T, BUF>(v, t, tw, buf);
     } else {
-        fft_forward<E, NCOL, T>(v, t, P, tw, buf);
+        fft_forward<E, NCOL, T, BUF>(v, t, P, tw, buf);
     }
 }
 

@@ -12,7 +12,7 @@ template <typename T>
 struct KernelSet {
     void (*x_fwd)(const T*, cpx<T>*, const cpx<T>*, double*, XArgs) = nullptr;
     void (*x_inv)(const cpx<T>*, T*, const cpx<T>*, XArgs) = nullptr;
-    void (*y_fwd)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;
+    void (*y_fwd)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;  // static lengths: C = ypass_cols(n)
     void (*y_inv)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;
     void (*z)(cpx<T>*, const cpx<T>*, const cpx<T>*, const T*, ZArgs) = nullptr;  // default z variant
 };
@@ -92,6 +92,17 @@ inline ZKernel<T> zvariant_for(int n, int E, bool joint) {
     return nullptr;
 }
 
+// True when length n has static kernels for type T.
+template <typename T>
+inline bool is_static_len(int n) {
+#define SBP_IS_STATIC(TT, TAG, N) \
+    if (std::is_same<T, TT>::value && n == N) return true;
+    SBP_N_LIST_F32(SBP_IS_STATIC)
+    SBP_N_LIST_F64(SBP_IS_STATIC)
+#undef SBP_IS_STATIC
+    return false;
+}
+
 // Kernels for a length-n transform with E elements per thread.
 template <typename T>
 inline KernelSet<T> kernels_for(int n, int E);
@@ -108,13 +119,13 @@ inline KernelSet<double> kernels_for<double>(int n, int E) {
 
 }  // namespace sbp
 
-#define SBP_SET_BODY(T, E, NS)             \
-    KernelSet<T> s;                        \
-    s.x_fwd = k_x_forward<T, E, NS>;       \
-    s.x_inv = k_x_inverse<T, E, NS>;       \
-    s.y_fwd = k_y_pass<T, E, false, NS>;   \
-    s.y_inv = k_y_pass<T, E, true, NS>;    \
-    s.z = k_z_pass<T, E, NS, false>;       \
+#define SBP_SET_BODY(T, E, NS)                                                  \
+    KernelSet<T> s;                                                             \
+    s.x_fwd = k_x_forward<T, E, NS>;                                            \
+    s.x_inv = k_x_inverse<T, E, NS>;                                            \
+    s.y_fwd = k_y_pass<T, E, false, NS, (NS > 0 ? ypass_cols(NS, sizeof(T) == 8) : 0)>; \
+    s.y_inv = k_y_pass<T, E, true, NS, (NS > 0 ? ypass_cols(NS, sizeof(T) == 8) : 0)>;  \
+    s.z = k_z_pass<T, E, NS, false>;                                            \
     return s;
 
 // Defines kernels_<TAG>_e<E>() (generic) in the including unit.

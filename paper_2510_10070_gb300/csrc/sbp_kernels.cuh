@@ -20,6 +20,13 @@
 namespace sbp {
 
 constexpr int kMaxThreads = 256;  // threads per block of every pass kernel
+// Resident blocks per SM the register allocation aims for (launch bounds):
+// the FP32 streaming x/y passes want 4 (≤ 64 registers) and the FP32 padded
+// z pass 3; FP64 and 24-element variants keep 2 so that they do not spill.
+template <typename T, int E>
+constexpr int min_blocks_xy() { return (sizeof(T) == 8 || E > 16) ? 2 : 4; }
+template <typename T, int E>
+constexpr int min_blocks_z() { return (sizeof(T) == 8 || E > 16) ? 2 : 3; }
 
 // Row stride (complex elements) of a [n][C] exchange buffer: one pad column
 // spreads consecutive rows over the banks; a single column needs none.
@@ -41,6 +48,7 @@ struct GreenFill {
     int per_block;
     int nx, ny;
     double Lx, Ly, L, s;
+    const double* s_dev;  // if set, s is read from device memory (batched executor)
 };
 
 struct XArgs {
@@ -70,6 +78,7 @@ struct ZArgs {
     int ny;
     int C;
     double L;           // L = Lz (enclosure of the truncated Green's function)
+    double kzc;         // (π / Lz)²: k_z,m² = kzc · m²
     double scale;       // 4πG / (nx·ny·2nz)
     int zero_k0;        // FP32 path: leave the (0,0) column to the FP64 side path
     const void* green;  // GreenT<T>[ny][h] at this solve's time
@@ -187,9 +196,10 @@ __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     const int total = h * gf.ny;
     const int q0 = block * gf.per_block;
     const int q1 = min(total, q0 + gf.per_block);
+    const double s = gf.s_dev != nullptr ? *gf.s_dev : gf.s;
     for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
         const int b = q / h, a = q - b * h;
-        const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, gf.s);
+        const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, s);
         tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
     }
 }
@@ -254,7 +264,7 @@ __device__ __forceinline__ void store_rows_from_smem(T* __restrict__ dst, const 
 // smem: tw[n] | C padded rows (exchange, then the paired spectrum Z)
 // ---------------------------------------------------------------------------
 template <typename T, int E, int NS>
-__global__ void __launch_bounds__(kMaxThreads) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
                                                            const cpx<T>* __restrict__ twg,
                                                            double* __restrict__ tile_sums, XArgs A) {
     if ((int)blockIdx.x < A.green_blocks) {  // FP64 Green's table, off the transform blocks
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_forward(const T* __restrict__
         }
     }
     __syncthreads();  // twiddles visible
-    const SmemCol<T> buf[1] = {{xb + c * RP, 0}};
+    const SmemRow<T> buf[1] = {{xb + c * RP, 0}};
     fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
     __syncthreads();
 #pragma unroll
@@ -337,10 +347,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_forward(const T* __restrict__
 // y pass (forward or inverse), in place: block = (a-tile of C columns, plane z).
 // smem: tw[n] | exchange [n][C+1]
 // ---------------------------------------------------------------------------
-template <typename T, int E, bool INV, int NS>
-__global__ void __launch_bounds__(kMaxThreads) k_y_pass(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A) {
+template <typename T, int E, bool INV, int NS, int CS = 0>
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A) {
+    // CS > 0: the column count is a compile-time constant (static lengths),
+    // so every exchange-buffer address is a base plus an immediate offset.
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
+    const int n = NS > 0 ? NS : A.P.n, Tf = NS > 0 ? NS / E : A.P.Tf;
+    const int C = CS > 0 ? CS : A.C;
     cpx<T>* tw = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* xb = tw + n;
     const int tid = threadIdx.x;
@@ -349,20 +362,30 @@ __global__ void __launch_bounds__(kMaxThreads) k_y_pass(cpx<T>* __restrict__ W, 
     const int c = tid % C, t = tid / C;
     const int a = blockIdx.x * C + c;
     const bool valid = a < A.h;
-    cpx<T>* col = W + (size_t)blockIdx.y * n * A.pitch + a;
+    const size_t step = (size_t)Tf * A.pitch;
+    cpx<T>* col = W + ((size_t)blockIdx.y * n + t) * A.pitch + a;
     cpx<T> v[1][E];
+    {
+        const cpx<T>* src = col;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        cpx<T> x = {(T)0, (T)0};
-        if (valid) x = col[(size_t)(t + Tf * e) * A.pitch];
-        v[0][e] = INV ? cconj(x) : x;
+        for (int e = 0; e < E; ++e, src += step) {
+            cpx<T> x = {(T)0, (T)0};
+            if (valid) x = *src;
+            v[0][e] = INV ? cconj(x) : x;
+        }
     }
     __syncthreads();  // twiddles visible
-    const SmemCol<T> buf[1] = {{xb + c, xstride(C)}};
-    fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+    if constexpr (CS > 0) {
+        const SmemCol<T, xstride(CS)> buf[1] = {{xb + c, 0}};
+        fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+    } else {
+        const SmemCol<T> buf[1] = {{xb + c, xstride(C)}};
+        fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+    }
     if (valid) {
+        cpx<T>* dst = col;
 #pragma unroll
-        for (int e = 0; e < E; ++e) col[(size_t)(t + Tf * e) * A.pitch] = INV ? cconj(v[0][e]) : v[0][e];
+        for (int e = 0; e < E; ++e, dst += step) *dst = INV ? cconj(v[0][e]) : v[0][e];
     }
 }
 
@@ -511,30 +534,85 @@ __global__ void __launch_bounds__(kMaxThreads) k_z_pass(cpx<T>* __restrict__ W, 
     }
 }
 
-// Padded variant: each column is one length-M = 2n transform.  Thread t holds
+// Columns per block of the y pass with static length N (compile-time):
+// 16 (FP32) or 8 (FP64), fewer when a column needs more than 256/16 threads.
+__host__ __device__ constexpr int ypass_cols(int N, bool f64) {
+    const int per_col = N / plan_E(N, f64);
+    const int cmax = f64 ? 8 : 16;
+    const int c = kMaxThreads / per_col;
+    return c < 1 ? 1 : (c < cmax ? c : cmax);
+}
+
+// Columns per block of the padded z kernel (compile-time): 16 (FP32) or 8
+// (FP64), fewer when a column needs more than 256/16 threads.
+__host__ __device__ constexpr int zpad_cols(int N, int E, bool f64) {
+    const int per_col = 2 * N / E;
+    const int cmax = f64 ? 8 : 16;
+    const int c = kMaxThreads / per_col;
+    return c < 1 ? 1 : (c < cmax ? c : cmax);
+}
+
+// Per-column factors of scale·Ĝ_eff(m) = Σ_branches F(parity)/(k² + k_z,m²):
+// for k ≠ 0, F = -scale·(1 ∓ e^{-kL}) (times ½ per branch when the Hermitian
+// partner's |k| differs); the k = 0 column is handled separately.
+template <typename T>
+struct GreenCoef {
+    T k2a, ae, ao, k2b, be, bo;
+    bool kzero, same, kill;
+};
+
+template <typename T>
+__device__ __forceinline__ GreenCoef<T> green_coef(const GreenT<T>& g, T scale, bool zero_k0) {
+    GreenCoef<T> q;
+    q.kzero = g.kzero != 0;
+    q.same = g.same != 0;
+    q.kill = zero_k0 && q.kzero;
+    const T w = q.same ? (T)1 : (T)0.5;
+    q.k2a = g.k2a;
+    q.ae = -scale * w * g.omEa;
+    q.ao = -scale * w * ((T)2 - g.omEa);
+    q.k2b = g.k2b;
+    q.be = -scale * w * g.omEb;
+    q.bo = -scale * w * ((T)2 - g.omEb);
+    return q;
+}
+
+// scale·Ĝ_eff at unsigned padded index m ∈ [0, 2N) with |signed m| = ms.
+template <typename T>
+__device__ __forceinline__ T green_factor(const GreenCoef<T>& q, int m, int ms, T kzc, T scale, T L2half) {
+    const T kz2 = kzc * (T)(ms * ms);  // k_z,m² = (π m / Lz)²
+    const bool odd = (m & 1) != 0;
+    if (q.kzero) {
+        if (q.kill) return (T)0;
+        if (m == 0) return scale * L2half;
+        return odd ? fast_div((T)-2 * scale, kz2) : (T)0;
+    }
+    T f = fast_div(odd ? q.ao : q.ae, q.k2a + kz2);
+    if (!q.same) f += fast_div(odd ? q.bo : q.be, q.k2b + kz2);
+    return f;
+}
+
+// Padded variant: each column is one length-M = 2N transform.  Thread t holds
 // elements t + Tf·e of the padded column; the zero half (e ≥ E/2) never enters
-// the pruned first stage, and of the inverse only the kept half (outputs < n)
+// the pruned first stage, and of the inverse only the kept half (outputs < N)
 // is stored, so the compiler drops the rest of the last stage.
-// smem: twM[M] | kz2[n+1] | green[C] | exchange [M][xstride(C)]
+// smem: twM[M] | green[C] | exchange [M][xstride(C)]
 template <typename T, int E, int N>
-__global__ void __launch_bounds__(kMaxThreads) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
-                                                          const cpx<T>* __restrict__ twMg, const T* __restrict__ kz2g,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
+                                                          const cpx<T>* __restrict__ twMg, const T* __restrict__ /*unused*/,
                                                           ZArgs A) {
     constexpr int M = 2 * N;
     constexpr int Tf = M / E;
+    constexpr int C = zpad_cols(N, E, sizeof(T) == 8);
+    constexpr int XS = xstride(C);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int C = A.C;
-    const int XS = xstride(C);
     cpx<T>* twM = reinterpret_cast<cpx<T>*>(smem_raw);
-    T* kz2 = reinterpret_cast<T*>(twM + M);
-    constexpr int kz2_slots = ((N + 1) * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
-    GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(kz2 + kz2_slots);
-    const int gm_bytes = ((C * (int)sizeof(GreenT<T>)) + 15) / 16 * 16;
+    GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(twM + M);
+    constexpr int gm_bytes = ((C * (int)sizeof(GreenT<T>)) + 15) / 16 * 16;
     cpx<T>* xb = reinterpret_cast<cpx<T>*>(reinterpret_cast<unsigned char*>(gm) + gm_bytes);
 
     const int tid = threadIdx.x;
     for (int i = tid; i < M; i += blockDim.x) twM[i] = twMg[i];
-    for (int i = tid; i <= N; i += blockDim.x) kz2[i] = kz2g[i];
     const int b = blockIdx.y;
     if (tid < C) {
         const int a = blockIdx.x * C + tid;
@@ -548,37 +626,40 @@ __global__ void __launch_bounds__(kMaxThreads) k_z_padded(cpx<T>* __restrict__ W
     const int c = tid % C, t = tid / C;
     const int a = blockIdx.x * C + c;
     const bool valid = a < A.h;
-    cpx<T>* col = W + (size_t)b * A.pitch + a;
     const size_t zstride = (size_t)A.ny * A.pitch;
+    const size_t step = (size_t)Tf * zstride;
+    cpx<T>* col = W + (size_t)b * A.pitch + a + (size_t)t * zstride;
     cpx<T> v[1][E];
+    {
+        const cpx<T>* src = col;
 #pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-        cpx<T> x = {(T)0, (T)0};
-        if (valid) x = col[(size_t)(t + Tf * e) * zstride];
-        v[0][e] = x;
+        for (int e = 0; e < E / 2; ++e, src += step) {
+            cpx<T> x = {(T)0, (T)0};
+            if (valid) x = *src;
+            v[0][e] = x;
+        }
     }
-    const SmemCol<T> buf[1] = {{xb + c, XS}};
+    const SmemCol<T, XS> buf[1] = {{xb + c, 0}};
     fft_static_padded<M, E, 1, T>(v, t, twM, buf);  // starts with a barrier: tables are visible
 
     {
-        const GreenT<T> g = gm[c];
         const T scale = (T)A.scale;
+        const GreenCoef<T> q = green_coef<T>(gm[c], scale, A.zero_k0 != 0);
+        const T kzc = (T)A.kzc;
         const T L2half = (T)(0.5 * A.L * A.L);
-        const bool kill = A.zero_k0 && g.kzero;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int m = t + Tf * e;
             const int ms = (m <= N) ? m : M - m;  // |signed m|
-            const T ge = green_eff_elem<T>(m, N, kz2[ms], g.k2a, g.omEa, g.k2b, g.omEb, g.kzero != 0, g.same != 0,
-                                           L2half);
-            const T f = kill ? (T)0 : ge * scale;
+            const T f = green_factor<T>(q, m, ms, kzc, scale, L2half);
             v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
         }
     }
     fft_static<M, E, 0, 1, T>(v, t, twM, buf);
     if (valid) {
+        cpx<T>* dst = col;
 #pragma unroll
-        for (int e = 0; e < E / 2; ++e) col[(size_t)(t + Tf * e) * zstride] = cconj(v[0][e]);
+        for (int e = 0; e < E / 2; ++e, dst += step) *dst = cconj(v[0][e]);
     }
 }
 
@@ -590,7 +671,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_z_padded(cpx<T>* __restrict__ W
 // smem: tw[n] | C padded rows (exchange)
 // ---------------------------------------------------------------------------
 template <typename T, int E, int NS>
-__global__ void __launch_bounds__(kMaxThreads) k_x_inverse(const cpx<T>* __restrict__ W, T* __restrict__ phi,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_inverse(const cpx<T>* __restrict__ W, T* __restrict__ phi,
                                                            const cpx<T>* __restrict__ twg, XArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
@@ -624,7 +705,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_x_inverse(const cpx<T>* __restr
         v[0][e] = cconj(z);
     }
     __syncthreads();  // twiddles visible
-    const SmemCol<T> buf[1] = {{xb + c * RP, 0}};
+    const SmemRow<T> buf[1] = {{xb + c * RP, 0}};
     fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
 
     // mean mode (FP32 path): the FP64 per-plane value, added as a double-float pair

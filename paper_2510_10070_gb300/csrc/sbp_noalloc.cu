@@ -126,7 +126,11 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     while (Cx > 1 && ((ny / 2) % Cx != 0 || xsm(Cx) > kSmemLimit)) --Cx;
     int Cy = std::min(std::max(1, std::min(16, kMaxThreads / py.Tf)), h);
     const auto ysm = [&](int C) { return (size_t)ny * cs + (size_t)ny * xstride(C) * cs; };
-    while (Cy > 1 && ysm(Cy) > kSmemLimit) --Cy;
+    if (is_static_len<float>(ny)) {
+        Cy = ypass_cols(ny, false);  // compiled into the static y kernel
+    } else {
+        while (Cy > 1 && ysm(Cy) > kSmemLimit) --Cy;
+    }
     int Cz = std::min(std::max(1, std::min(16, kMaxThreads / (2 * pz.Tf))), h);
     const auto zsm = [&](int C) {
         return 2 * (size_t)nz * cs + (((size_t)(nz + 1) * sizeof(float) + 15) / 16 * 16) +
@@ -247,6 +251,7 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     za.ny = ny;
     za.C = Cz;
     za.L = Lz;
+    za.kzc = (M_PI / Lz) * (M_PI / Lz);
     za.scale = 4.0 * M_PI * G / ((double)nx * ny * 2.0 * nz);
     za.zero_k0 = 1;
     za.green = base + oGr;

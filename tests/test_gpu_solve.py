@@ -88,6 +88,29 @@ def test_in_place_and_batched_match_single(sbp, dtype):
     assert torch.equal(inplace, singles[1])
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batched_uneven_boxes_repeated_calls(sbp, dtype):
+    # cached executor: later calls change only the shear times
+    import torch
+
+    shapes = [(64, 64, 32), (32, 32, 16), (48, 24, 12), (96, 64, 48), (16, 16, 8)]
+    rng = np.random.default_rng(17)
+    boxes = [W.Box(nx, ny, nz, 2.0, 3.0, 1.5, q=1.5 if i % 2 == 0 else 1.0) for i, (nx, ny, nz) in enumerate(shapes)]
+    plans = [_plan(sbp, b, dtype) for b in boxes]
+    rhos = [to_dev(rng.standard_normal((b.nz, b.ny, b.nx)), dtype) for b in boxes]
+    outs = [torch.empty_like(r) for r in rhos]
+    for ts in ([0.1, 2.0, -1.0, 3.3, 7.7], [5.0, 0.0, 0.4, -2.2, 1.9], [0.1, 2.0, -1.0, 3.3, 7.7]):
+        sbp.solve_batched(plans, rhos, outs, ts)
+        singles = [plans[i].solve(rhos[i], t=ts[i]) for i in range(len(plans))]
+        torch.cuda.synchronize()
+        for i in range(len(plans)):
+            assert torch.equal(outs[i], singles[i]), (i, ts)
+    # one box against the oracle
+    want = O.solve(as_input(rhos[3].double().cpu().numpy(), dtype), _params(boxes[3]), -2.2)
+    sbp.solve_batched(plans, rhos, outs, [5.0, 0.0, 0.4, -2.2, 1.9])
+    assert rel_l2(outs[3].double().cpu().numpy(), want) <= TOL[dtype]
+
+
 def test_partial_overlap_rejected(sbp):
     import torch
 
