@@ -138,7 +138,14 @@ enum {
      * halves in two thread groups with the default elements per thread.
      * Variants 1-3 exist for the common lengths only
      * (SBP_ERR_UNSUPPORTED_SIZE otherwise, plan unchanged). */
-    SBP_OPT_Z_VARIANT = 1
+    SBP_OPT_Z_VARIANT = 1,
+    /* How a solve runs the x and y transforms (same result, different speed):
+     * 0 = automatic (the default); 1 = separate x and y passes; 2 = fused
+     * plane kernels, one z-plane per thread-block cluster, sized for one CTA
+     * per SM; 3 = the same sized for two CTAs per SM.  Variants 2 and 3 exist
+     * for square planes of the common sizes only (SBP_ERR_UNSUPPORTED_SIZE
+     * otherwise, plan unchanged). */
+    SBP_OPT_XY_PASSES = 2
 };
 
 /* sbp_plan_set_option — set a plan option (see the enum above).  Unknown

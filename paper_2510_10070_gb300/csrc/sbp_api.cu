@@ -91,6 +91,12 @@ struct sbp_plan_s {
     bool z_padded = false;     // the chosen kernel takes the length-2nz twiddle table
     void* z_fn = nullptr;      // the z-pass kernel of the chosen variant
     int green_blocks = 0;      // x-forward blocks that fill the Green's table
+    // fused xy plane kernels (square planes with a built kernel), used by solves
+    bool xy_fused = false;
+    void* xy_fwd = nullptr;
+    void* xy_inv = nullptr;
+    int xy_cluster = 0, xy_threads = 0, xy_green_ctas = 0;
+    size_t xy_smem_fwd = 0, xy_smem_inv = 0;
     // device memory
     void* W = nullptr;        // half spectrum
     void* tables = nullptr;   // twiddles, kz², c00, tile sums, vk0
@@ -193,6 +199,43 @@ bool configure_z(sbp_plan_s* p, int variant) {
     return true;
 }
 
+// xy pass variant (SBP_OPT_XY_PASSES): 0 = automatic, 1 = separate x and y
+// passes, 2 = fused plane kernels with one CTA per SM, 3 = fused with two
+// CTAs per SM.  Returns false, leaving the plan unchanged, when unavailable.
+template <typename T>
+bool configure_xy(sbp_plan_s* p, int variant) {
+    if (variant == 0) {
+        // measured on GB300: the fused plane kernels win for the small FP32
+        // planes only; larger planes stream better through the separate passes
+        const bool small = !f64_of(p) && p->nx == p->ny && p->nx <= 96;
+        return (small && configure_xy<T>(p, 2)) || configure_xy<T>(p, 1);
+    }
+    if (variant == 1) {
+        p->xy_fused = false;
+        return true;
+    }
+    if (p->nx != p->ny || (variant != 2 && variant != 3)) return false;
+    const XYKernels<T> k = xy_kernels_for<T>(p->nx, variant - 1);
+    if (!k.fwd || !k.inv || k.smem_fwd > kSmemBudget || k.smem_inv > kSmemBudget) return false;
+    if (cudaFuncSetAttribute(k.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess ||
+        cudaFuncSetAttribute(k.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    // the FP32 mean-mode tile sums hold one value per CTA of a plane
+    if ((long long)p->nz * k.cluster > (long long)p->xf.grid.x) return false;
+    p->xy_fused = true;
+    p->xy_fwd = reinterpret_cast<void*>(k.fwd);
+    p->xy_inv = reinterpret_cast<void*>(k.inv);
+    p->xy_cluster = k.cluster;
+    p->xy_threads = k.threads;
+    p->xy_smem_fwd = k.smem_fwd;
+    p->xy_smem_inv = k.smem_inv;
+    const int per = k.threads * k.cluster;
+    p->xy_green_ctas = (p->h * p->ny + per - 1) / per * k.cluster;
+    return true;
+}
+
 template <typename T>
 bool configure(sbp_plan_s* p) {
     const bool f64 = std::is_same<T, double>::value;
@@ -241,6 +284,7 @@ bool configure(sbp_plan_s* p) {
     // Green's-table blocks in front of the x-forward grid: one table entry per
     // thread, so that the FP64 work spreads over as many SMs as possible.
     p->green_blocks = (p->h * p->ny + p->xf.threads - 1) / p->xf.threads;
+    configure_xy<T>(p, 0);
     return e == cudaSuccess && configure_z<T>(p, 0);
 }
 
@@ -427,7 +471,7 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     a.zero_k0 = f32 ? 1 : 0;
     a.green = p->green;
     a.tile_sums = p->tile_sums;
-    a.tiles_per_plane = (p->ny / 2) / p->xf.C;
+    a.tiles_per_plane = p->xy_fused ? p->xy_cluster : (p->ny / 2) / p->xf.C;
     a.c00 = p->c00;
     a.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
     a.vk0 = (f32 && with_k0) ? p->vk0 : nullptr;
@@ -497,9 +541,61 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
     return cudaGetLastError() == cudaSuccess ? SBP_OK : SBP_ERR_CUDA;
 }
 
+// Launch a fused xy plane kernel: one cluster of xy_cluster CTAs per z-plane.
+template <typename K, typename... Args>
+sbp_status launch_xy(const sbp_plan_s* p, K kernel, int ctas, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ctas, 1, 1);
+    cfg.blockDim = dim3((unsigned)p->xy_threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p->xy_cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, kernel, args...) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    return SBP_OK;
+}
+
+template <typename T>
+sbp_status solve_fused_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
+                         const double* s_dev) {
+    const bool f32 = !f64_of(p);
+    XYArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.pitch = p->pitch;
+    a.green_ctas = p->xy_green_ctas;
+    a.gf = make_green_fill(p, t, p->xy_green_ctas);
+    a.gf.s_dev = s_dev;
+    a.tile_sums = f32 ? p->tile_sums : nullptr;
+    a.vk0 = nullptr;
+    using FwdK = void (*)(const T*, cpx<T>*, const cpx<T>*, XYArgs);
+    using InvK = void (*)(const cpx<T>*, T*, const cpx<T>*, XYArgs);
+    cpx<T>* W = static_cast<cpx<T>*>(p->W);
+    const cpx<T>* tw = static_cast<const cpx<T>*>(p->tw_x);
+    sbp_status s = launch_xy(p, reinterpret_cast<FwdK>(p->xy_fwd), p->xy_green_ctas + p->nz * p->xy_cluster,
+                             p->xy_smem_fwd, st, static_cast<const T*>(rho), W, tw, a);
+    if (s != SBP_OK) return s;
+    if ((s = launch_stage<T>(p, SBP_STAGE_Z_CONVOLVE, p->W, p->W, t, st, true)) != SBP_OK) return s;
+    XYArgs b = a;
+    b.green_ctas = 0;
+    b.gf.tab = nullptr;
+    b.tile_sums = nullptr;
+    b.vk0 = f32 ? p->vk0 : nullptr;
+    return launch_xy(p, reinterpret_cast<InvK>(p->xy_inv), p->nz * p->xy_cluster, p->xy_smem_inv, st,
+                     static_cast<const cpx<T>*>(p->W), static_cast<T*>(phi), tw, b);
+}
+
 template <typename T>
 sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
                    const double* s_dev = nullptr) {
+    if (p->xy_fused) return solve_fused_t<T>(p, rho, phi, t, st, s_dev);
     sbp_status s;
     if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true, s_dev)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Y_FORWARD, p->W, p->W, t, st, true)) != SBP_OK) return s;
@@ -850,6 +946,14 @@ const char* sbp_status_string(sbp_status s) {
 
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
+    if (option == SBP_OPT_XY_PASSES) {
+        const int v = (int)value;
+        if ((double)v != value || v < 0 || v > 3) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        const bool ok = f64_of(p) ? configure_xy<double>(p, v) : configure_xy<float>(p, v);
+        return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
+    }
     if (option == SBP_OPT_Z_VARIANT) {
         const int v = (int)value;
         if ((double)v != value || v < 0 || v > 4) return SBP_ERR_INVALID_ARG;

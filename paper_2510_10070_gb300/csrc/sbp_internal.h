@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "sbp_kernels.cuh"
+#include "sbp_xy.cuh"
 
 namespace sbp {
 
@@ -90,6 +91,53 @@ inline ZKernel<T> zvariant_for(int n, int E, bool joint) {
     SBP_ZVAR_LIST(SBP_MATCH_ZVAR)
 #undef SBP_MATCH_ZVAR
     return nullptr;
+}
+
+// Fused xy kernels for square planes nx = ny = N (one z-plane per cluster).
+template <typename T>
+struct XYKernels {
+    void (*fwd)(const T*, cpx<T>*, const cpx<T>*, XYArgs) = nullptr;
+    void (*inv)(const cpx<T>*, T*, const cpx<T>*, XYArgs) = nullptr;
+    int cluster = 0, threads = 0;
+    size_t smem_fwd = 0, smem_inv = 0;
+};
+// (type, N, variant): variant 1 = one CTA per SM, 2 = two CTAs per SM.
+#define SBP_XY_LIST(X) X(float, f32, 64, 1) X(float, f32, 96, 1) X(float, f32, 128, 1) X(float, f32, 192, 1) \
+    X(float, f32, 256, 1) X(float, f32, 512, 1) X(double, f64, 64, 1) X(double, f64, 128, 1) X(double, f64, 256, 1) \
+    X(float, f32, 128, 2) X(float, f32, 192, 2) X(float, f32, 256, 2) X(float, f32, 512, 2)
+#define SBP_DECLARE_XY(T, TAG, N, V) XYKernels<T> xy_##TAG##_n##N##_v##V();
+SBP_XY_LIST(SBP_DECLARE_XY)
+#define SBP_DEFINE_XY(T, TAG, N, V)                                \
+    XYKernels<T> xy_##TAG##_n##N##_v##V() {                        \
+        constexpr int CL = xy_cluster<T, N, (V == 1 ? kXYSmemOnePerSM : kXYSmemTwoPerSM)>(); \
+        using SH = XYShape<T, N, CL>;                              \
+        XYKernels<T> k;                                            \
+        k.fwd = k_xy_forward<T, N, CL>;                            \
+        k.inv = k_xy_inverse<T, N, CL>;                            \
+        k.cluster = CL;                                            \
+        k.threads = SH::NT;                                        \
+        k.smem_fwd = SH::smem_fwd;                                 \
+        k.smem_inv = SH::smem_inv;                                 \
+        return k;                                                  \
+    }
+
+template <typename T>
+inline XYKernels<T> xy_kernels_for(int n, int variant) {
+#define SBP_MATCH_XY(TT, TAG, N, V)                                               \
+    if (std::is_same<T, TT>::value && n == N && variant == V) {                   \
+        auto k = xy_##TAG##_n##N##_v##V();                                        \
+        XYKernels<T> r;                                                           \
+        r.fwd = reinterpret_cast<decltype(r.fwd)>(k.fwd);                         \
+        r.inv = reinterpret_cast<decltype(r.inv)>(k.inv);                         \
+        r.cluster = k.cluster;                                                    \
+        r.threads = k.threads;                                                    \
+        r.smem_fwd = k.smem_fwd;                                                  \
+        r.smem_inv = k.smem_inv;                                                  \
+        return r;                                                                 \
+    }
+    SBP_XY_LIST(SBP_MATCH_XY)
+#undef SBP_MATCH_XY
+    return XYKernels<T>{};
 }
 
 // True when length n has static kernels for type T.

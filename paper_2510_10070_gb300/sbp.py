@@ -46,6 +46,7 @@ class Stage(IntEnum):
 
 class Option(IntEnum):
     Z_VARIANT = 1
+    XY_PASSES = 2
 
 
 class SbpError(RuntimeError):

@@ -67,6 +67,41 @@ def test_random_boxes(sbp, shape, dtype):
         assert rel_l2(got, want) <= TOL[dtype], (shape, t)
 
 
+# square planes run the fused xy plane kernels (one z-plane per CTA cluster)
+SQUARE = [(64, 64, 16), (96, 96, 12), (128, 128, 8), (192, 192, 6), (256, 256, 4), (512, 512, 2)]
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("shape", SQUARE)
+def test_fused_plane_boxes(sbp, shape, dtype):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + nz)
+    box = W.Box(nx, ny, nz, 3.0, 3.0, 1.5, q=1.5, Omega=0.9, G=0.8)
+    rho = rng.standard_normal((nz, ny, nx)) + 0.5
+    for t in (0.0, 0.83):
+        got = _gpu_solve(sbp, box, rho, t, dtype)
+        want = O.solve(as_input(rho, dtype), _params(box), t)
+        assert rel_l2(got, want) <= TOL[dtype], (shape, t)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("shape", SQUARE)
+def test_xy_pass_variants(sbp, shape, variant):
+    # every xy-pass variant gives the oracle's answer (FP32)
+    nx, ny, nz = shape
+    box = W.Box(nx, ny, nz, 3.0, 3.0, 1.5, q=1.5, Omega=0.9, G=0.8)
+    plan = _plan(sbp, box, 1)
+    try:
+        plan.set_option(sbp.Option.XY_PASSES, variant)
+    except sbp.SbpError as err:
+        assert err.status == sbp.Status.UNSUPPORTED_SIZE
+        pytest.skip(f"xy variant {variant} not built for {shape}")
+    rho = np.random.default_rng(nx * 3 + nz).standard_normal((nz, ny, nx)) + 0.5
+    got = plan.solve(to_dev(rho, 1), t=0.61).double().cpu().numpy()
+    want = O.solve(as_input(rho, 1), _params(box), 0.61)
+    assert rel_l2(got, want) <= TOL[1]
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_in_place_and_batched_match_single(sbp, dtype):
     import torch
