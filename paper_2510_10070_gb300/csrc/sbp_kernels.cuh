@@ -114,8 +114,14 @@ __device__ __forceinline__ void mean_mode_fp64(const ZArgs& A, int nz, double* s
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T fast_div(T a, T b);
+// FP32: a · rcp.approx(b) (relative error about 2^-23; the divisors here are
+// positive and far from the denormal and overflow ranges)
 template <>
-__device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float fast_div<float>(float a, float b) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return a * r;
+}
 template <>
 __device__ __forceinline__ double fast_div<double>(double a, double b) { return a / b; }
 
@@ -553,8 +559,9 @@ __host__ __device__ constexpr int zpad_cols(int N, int E, bool f64) {
 }
 
 // Per-column factors of scale·Ĝ_eff(m) = Σ_branches F(parity)/(k² + k_z,m²):
-// for k ≠ 0, F = -scale·(1 ∓ e^{-kL}) (times ½ per branch when the Hermitian
-// partner's |k| differs); the k = 0 column is handled separately.
+// for k ≠ 0, F = -scale·(1 ∓ e^{-kL}) for the mode and its Hermitian partner,
+// weighted ½ + ½ when their |k| differ and 1 + 0 otherwise; the k = 0 column
+// is handled separately.
 template <typename T>
 struct GreenCoef {
     T k2a, ae, ao, k2b, be, bo;
@@ -567,29 +574,30 @@ __device__ __forceinline__ GreenCoef<T> green_coef(const GreenT<T>& g, T scale, 
     q.kzero = g.kzero != 0;
     q.same = g.same != 0;
     q.kill = zero_k0 && q.kzero;
-    const T w = q.same ? (T)1 : (T)0.5;
+    // the second branch carries weight 0 when the partner has the same |k|
+    const T wa = q.same ? (T)1 : (T)0.5;
+    const T wb = q.same ? (T)0 : (T)0.5;
     q.k2a = g.k2a;
-    q.ae = -scale * w * g.omEa;
-    q.ao = -scale * w * ((T)2 - g.omEa);
-    q.k2b = g.k2b;
-    q.be = -scale * w * g.omEb;
-    q.bo = -scale * w * ((T)2 - g.omEb);
+    q.ae = -scale * wa * g.omEa;
+    q.ao = -scale * wa * ((T)2 - g.omEa);
+    q.k2b = q.kzero ? (T)1 : g.k2b;  // keep the unused division finite
+    q.be = -scale * wb * g.omEb;
+    q.bo = -scale * wb * ((T)2 - g.omEb);
     return q;
 }
 
 // scale·Ĝ_eff at unsigned padded index m ∈ [0, 2N) with |signed m| = ms.
+// Branch-free: lanes of a warp hold different columns, so per-column cases
+// are selected, not branched on (both branches are cheap).
 template <typename T>
 __device__ __forceinline__ T green_factor(const GreenCoef<T>& q, int m, int ms, T kzc, T scale, T L2half) {
     const T kz2 = kzc * (T)(ms * ms);  // k_z,m² = (π m / Lz)²
     const bool odd = (m & 1) != 0;
-    if (q.kzero) {
-        if (q.kill) return (T)0;
-        if (m == 0) return scale * L2half;
-        return odd ? fast_div((T)-2 * scale, kz2) : (T)0;
-    }
-    T f = fast_div(odd ? q.ao : q.ae, q.k2a + kz2);
-    if (!q.same) f += fast_div(odd ? q.bo : q.be, q.k2b + kz2);
-    return f;
+    // k ≠ 0: one or two screened terms (the second is zero when the partner's |k| is the same)
+    const T f = fast_div(odd ? q.ao : q.ae, q.k2a + kz2) + fast_div(odd ? q.bo : q.be, q.k2b + kz2);
+    // k = 0: L²/2 at m = 0, -2/k_z² for odd m, 0 for even m ≠ 0
+    const T f0 = (m == 0) ? scale * L2half : (odd ? fast_div((T)-2 * scale, kz2) : (T)0);
+    return q.kill ? (T)0 : (q.kzero ? f0 : f);
 }
 
 // Padded variant: each column is one length-M = 2N transform.  Thread t holds
@@ -647,12 +655,26 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padde
         const GreenCoef<T> q = green_coef<T>(gm[c], scale, A.zero_k0 != 0);
         const T kzc = (T)A.kzc;
         const T L2half = (T)(0.5 * A.L * A.L);
+        // Tf is even, so every element of this thread has the parity of t.
+        static_assert(Tf % 2 == 0 && (C * Tf) % 32 == 0, "padded z kernel shape");
+        if (__all_sync(0xffffffffu, q.same && !q.kzero)) {
+            // the common case, uniform across the warp: one screened term
+            const T num = (t & 1) ? q.ao : q.ae;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int m = t + Tf * e;
-            const int ms = (m <= N) ? m : M - m;  // |signed m|
-            const T f = green_factor<T>(q, m, ms, kzc, scale, L2half);
-            v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            for (int e = 0; e < E; ++e) {
+                const int m = t + Tf * e;
+                const int ms = (m <= N) ? m : M - m;  // |signed m|
+                const T f = fast_div(num, q.k2a + kzc * (T)(ms * ms));
+                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int m = t + Tf * e;
+                const int ms = (m <= N) ? m : M - m;
+                const T f = green_factor<T>(q, m, ms, kzc, scale, L2half);
+                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            }
         }
     }
     fft_static<M, E, 0, 1, T>(v, t, twM, buf);
