@@ -89,6 +89,27 @@ def oracle_cost(box):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing (replicas: every rank solves its own copy of the batch)
+# ---------------------------------------------------------------------------
+
+def max_over_ranks(ms, device=None):
+    """The slowest rank's time; each rank passes its own (1 rank: unchanged)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, ms_max):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
@@ -264,14 +285,10 @@ def main():
             step()
         end.record(stream)
         barrier()
-    ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end), device=dev)
     ms_per_step = ms / args.steps
     nbox = len(boxes)
-    value = world * nbox * args.steps / (ms / 1e3)
+    value = job_rate(nbox, args.steps, world, ms)
     cells = sum(b.cells for b in boxes)
     balg = sum(alg_bytes(b, rb) for b in boxes)
 
@@ -297,7 +314,7 @@ def main():
         e2e_step()
     e2.record(stream)
     barrier()
-    e2e_value = world * nbox * e2e_steps / (s2.elapsed_time(e2) / 1e3)
+    e2e_value = job_rate(nbox, e2e_steps, world, max_over_ranks(s2.elapsed_time(e2), device=dev))
 
     # dominant kernel: the z pass of the largest box, timed alone with CUDA
     # events on the launching stream, on the same data
