@@ -65,6 +65,25 @@ def build_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def recorded_traffic(kernel_name):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    record, or None when the kernel sources changed since it was taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "z_pass_traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for name in ("sbp_kernels.cuh", "sbp_fft.cuh"):
+            with open(os.path.join(ROOT, "paper_2510_10070_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha256") != h.hexdigest() or rec.get("kernel") != kernel_name:
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
 def alg_bytes(box, rb):
     """B_alg of one solve: read ρ, write φ, and the half spectrum written by
     the forward passes, read and written by the z pass and read by the
@@ -337,9 +356,12 @@ def main():
     peaks, peak_src = measured_peaks()
     zbytes = z_pass_bytes(boxes[big], rb)
     z_gbs = zbytes / (z_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"k_z_padded/k_z_pass, {boxes[big].nx}x{boxes[big].ny}x{boxes[big].nz}",
+    zb = boxes[big]
+    zname = f"k_z_padded<{'float' if dt == 1 else 'double'}, {16 if dt == 1 else 8}, {zb.nz}>"
+    roofline = {"bound": "hbm", "kernel": f"{zname} (z pass), {zb.nx}x{zb.ny}x{zb.nz}",
                 "achieved": z_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": z_gbs / peaks["hbm_gbs"],
-                "traffic": None, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": recorded_traffic(zname), "alg_bytes_per_launch": zbytes,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "step_alg_gbs": balg / (ms_per_step / 1e3) / 1e9,
                 "step_frac": balg / (ms_per_step / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
