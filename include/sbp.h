@@ -145,13 +145,30 @@ enum {
      * per SM; 3 = the same sized for two CTAs per SM.  Variants 2 and 3 exist
      * for square planes of the common sizes only (SBP_ERR_UNSUPPORTED_SIZE
      * otherwise, plan unchanged). */
-    SBP_OPT_XY_PASSES = 2
+    SBP_OPT_XY_PASSES = 2,
+    /* 0 = the y passes load their column tiles with TMA bulk-tensor copies on
+     * an mbarrier where available (the default); 1 = plain per-thread loads. */
+    SBP_OPT_Y_TMA = 3,
+    /* Clock cycles a kernel may wait for an asynchronous copy before it gives
+     * up, records the timeout in the plan's status word and returns
+     * (default 2e9, about one second). */
+    SBP_OPT_SPIN_BUDGET = 4,
+    /* Test switch: 1 makes the TMA kernels arm no copy, so that their bounded
+     * waits run out (the results are then undefined and
+     * sbp_plan_sync_status reports SBP_ERR_DEVICE_TIMEOUT); 0 restores. */
+    SBP_OPT_DEBUG_WITHHOLD_COPY = 5
 };
 
 /* sbp_plan_set_option — set a plan option (see the enum above).  Unknown
  * options or values return SBP_ERR_INVALID_ARG.  Not to be called while a
  * solve of this plan is in flight. */
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value);
+
+/* sbp_plan_sync_status — synchronise `stream` and report device-side
+ * failures of this plan's kernels since the last call: SBP_ERR_DEVICE_TIMEOUT
+ * when a bounded wait gave up (the status word is then cleared), SBP_OK
+ * otherwise. */
+sbp_status sbp_plan_sync_status(sbp_plan p, void* stream);
 
 /* sbp_plan_info — sizes of a plan.  Any output pointer may be NULL.
  * spectrum_pitch: complex elements per (z, y) row of the half spectrum

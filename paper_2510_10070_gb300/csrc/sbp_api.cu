@@ -1,5 +1,7 @@
 // sbp_api.cu — plans, plan-time tables, launch configuration and the C ABI.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -111,6 +113,13 @@ struct sbp_plan_s {
     double* tile_sums = nullptr;
     double* vk0 = nullptr;    // FP64 mean-mode potential per plane (FP32 path)
     void* green = nullptr;    // GreenT<T>[ny][nx/2+1] for the current solve
+    int* err = nullptr;       // device status word: 1 after a bounded wait gave up
+    // TMA y passes (static ny): tile loads of the half spectrum
+    bool y_tma = false;
+    CUtensorMap tmap_y;
+    size_t y_tma_smem = 0;
+    long long spin_budget = 2000000000LL;  // clock cycles per bounded wait (about 1 s)
+    int withhold = 0;                      // test switch (SBP_OPT_DEBUG_WITHHOLD_COPY)
 };
 
 namespace {
@@ -145,6 +154,61 @@ size_t xfwd_smem(int n, int C) {
 template <typename T>
 size_t xinv_smem(int n, int C) {
     return (size_t)n * sizeof(cpx<T>) + (size_t)C * padded_row(n) * sizeof(cpx<T>);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// TMA y passes: a 2D map over a half spectrum viewed as rows of 2·pitch
+// reals (one row per (z, y)), boxes of 2·C reals by min(ny, 256) rows.
+template <typename T>
+bool encode_ymap(const sbp_plan_s* p, void* spectrum, CUtensorMap* map) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)2 * p->pitch, (cuuint64_t)p->nz * p->ny};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * p->pitch * sizeof(T)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * p->yp.C), (cuuint32_t)std::min(p->ny, 256)};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, spectrum,
+               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T>
+bool configure_ytma(sbp_plan_s* p, bool enable) {
+    p->y_tma = false;
+    if (!enable || !is_static_len<T>(p->ny) || p->W == nullptr) return !enable;
+    const KernelSet<T> ky = kernels_for<T>(p->ny, p->py.E);
+    auto enc = tensor_map_encoder();
+    if (!ky.y_fwd_tma || !ky.y_inv_tma || !enc) return false;
+    const int C = p->yp.C;
+    const size_t smem = align_up((size_t)p->ny * C * sizeof(cpx<T>), 16) + (size_t)p->ny * sizeof(cpx<T>) + 16;
+    if (smem > kSmemBudget || (2 * C * sizeof(T)) % 16 != 0) return false;
+    if (!encode_ymap<T>(p, p->W, &p->tmap_y)) return false;
+    if (cudaFuncSetAttribute(ky.y_fwd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(ky.y_inv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    p->y_tma_smem = smem;
+    p->y_tma = true;
+    return true;
 }
 
 // z-pass variant (SBP_OPT_Z_VARIANT): 0 = automatic (3 where built, else 4);
@@ -348,6 +412,7 @@ sbp_status upload_tables(sbp_plan_s* p) {
     const size_t o_c00 = take((2 * (size_t)p->nz) * sizeof(double));
     const size_t o_ts = take((size_t)tiles * sizeof(double));
     const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
+    const size_t o_err = take(sizeof(int));
     const size_t o_green = take((size_t)p->h * p->ny * sizeof(GreenT<T>));
     p->tables_bytes = off;
     if (cudaMalloc(&p->tables, off) != cudaSuccess) {
@@ -363,6 +428,7 @@ sbp_status upload_tables(sbp_plan_s* p) {
     p->c00 = reinterpret_cast<double*>(base + o_c00);
     p->tile_sums = reinterpret_cast<double*>(base + o_ts);
     p->vk0 = reinterpret_cast<double*>(base + o_vk0);
+    p->err = reinterpret_cast<int*>(base + o_err);
     p->tw_M = base + o_twM;
     p->green = base + o_green;
 
@@ -447,6 +513,14 @@ XArgs make_xargs(const sbp_plan_s* p) {
     a.vk0 = nullptr;
     return a;
 }
+TmaCtl make_tmactl(const sbp_plan_s* p) {
+    TmaCtl c;
+    c.err = p->err;
+    c.budget = p->spin_budget;
+    c.withhold = p->withhold;
+    return c;
+}
+
 template <typename T>
 YArgs make_yargs(const sbp_plan_s* p) {
     YArgs a;
@@ -504,8 +578,20 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
             break;
         }
         case SBP_STAGE_Y_FORWARD:
-            ky.y_fwd<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
-                                                                   make_yargs<T>(p));
+            if (p->y_tma) {
+                // the plan's map covers its own workspace; other buffers get their own
+                CUtensorMap local;
+                const CUtensorMap* map = &p->tmap_y;
+                if (out != p->W) {
+                    if (!encode_ymap<T>(p, out, &local)) return SBP_ERR_INVALID_ARG;
+                    map = &local;
+                }
+                ky.y_fwd_tma<<<p->yp.grid, p->yp.threads, p->y_tma_smem, st>>>(
+                    W, static_cast<const cpx<T>*>(p->tw_y), make_yargs<T>(p), make_tmactl(p), *map);
+            } else {
+                ky.y_fwd<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
+                                                                       make_yargs<T>(p));
+            }
             break;
         case SBP_STAGE_GREEN_FILL: {
             const int blocks = (p->h * p->ny + 255) / 256;
@@ -519,8 +605,20 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
                 static_cast<const T*>(p->kz2), make_zargs<T>(p, fused));
             break;
         case SBP_STAGE_Y_INVERSE:
-            ky.y_inv<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
-                                                                   make_yargs<T>(p));
+            if (p->y_tma) {
+                // the plan's map covers its own workspace; other buffers get their own
+                CUtensorMap local;
+                const CUtensorMap* map = &p->tmap_y;
+                if (out != p->W) {
+                    if (!encode_ymap<T>(p, out, &local)) return SBP_ERR_INVALID_ARG;
+                    map = &local;
+                }
+                ky.y_inv_tma<<<p->yp.grid, p->yp.threads, p->y_tma_smem, st>>>(
+                    W, static_cast<const cpx<T>*>(p->tw_y), make_yargs<T>(p), make_tmactl(p), *map);
+            } else {
+                ky.y_inv<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
+                                                                       make_yargs<T>(p));
+            }
             break;
         case SBP_STAGE_X_INVERSE: {
             XArgs a = make_xargs<T>(p);
@@ -827,6 +925,11 @@ sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz, double Lx, dou
         free_plan(p);
         return s;
     }
+    if (f64) {
+        configure_ytma<double>(p, true);
+    } else {
+        configure_ytma<float>(p, true);
+    }
     *out = p;
     return SBP_OK;
 }
@@ -946,6 +1049,24 @@ const char* sbp_status_string(sbp_status s) {
 
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
+    if (option == SBP_OPT_Y_TMA) {
+        if (value != 0.0 && value != 1.0) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        const bool want = (value == 0.0);
+        const bool ok = f64_of(p) ? configure_ytma<double>(p, want) : configure_ytma<float>(p, want);
+        return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
+    }
+    if (option == SBP_OPT_SPIN_BUDGET) {
+        if (!(value >= 1000.0 && value <= 1e12)) return SBP_ERR_INVALID_ARG;
+        p->spin_budget = (long long)value;
+        return SBP_OK;
+    }
+    if (option == SBP_OPT_DEBUG_WITHHOLD_COPY) {
+        if (value != 0.0 && value != 1.0) return SBP_ERR_INVALID_ARG;
+        p->withhold = (int)value;
+        return SBP_OK;
+    }
     if (option == SBP_OPT_XY_PASSES) {
         const int v = (int)value;
         if ((double)v != value || v < 0 || v > 3) return SBP_ERR_INVALID_ARG;
@@ -963,6 +1084,28 @@ sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
         return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
     }
     return SBP_ERR_INVALID_ARG;
+}
+
+sbp_status sbp_plan_sync_status(sbp_plan p, void* stream) {
+    if (!p) return SBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int flag = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess ||
+        cudaMemcpy(&flag, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    if (flag != 0) {
+        const int zero = 0;
+        if (cudaMemcpy(p->err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return SBP_ERR_CUDA;
+        }
+        return SBP_ERR_DEVICE_TIMEOUT;
+    }
+    return SBP_OK;
 }
 
 sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int* spectrum_pitch,

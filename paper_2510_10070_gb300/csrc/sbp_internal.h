@@ -14,6 +14,9 @@ struct KernelSet {
     void (*x_fwd)(const T*, cpx<T>*, const cpx<T>*, double*, XArgs) = nullptr;
     void (*x_inv)(const cpx<T>*, T*, const cpx<T>*, XArgs) = nullptr;
     void (*y_fwd)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;  // static lengths: C = ypass_cols(n)
+    // TMA y passes (static lengths only; C = ypass_cols(n))
+    void (*y_fwd_tma)(cpx<T>*, const cpx<T>*, YArgs, TmaCtl, const CUtensorMap) = nullptr;
+    void (*y_inv_tma)(cpx<T>*, const cpx<T>*, YArgs, TmaCtl, const CUtensorMap) = nullptr;
     void (*y_inv)(cpx<T>*, const cpx<T>*, YArgs) = nullptr;
     void (*z)(cpx<T>*, const cpx<T>*, const cpx<T>*, const T*, ZArgs) = nullptr;  // default z variant
 };
@@ -180,5 +183,10 @@ inline KernelSet<double> kernels_for<double>(int n, int E) {
 #define SBP_DEFINE_SET(T, TAG, E) \
     KernelSet<T> kernels_##TAG##_e##E() { SBP_SET_BODY(T, E, 0) }
 // Defines kernels_<TAG>_n<N>() (static length N) in the including unit.
-#define SBP_DEFINE_SET_N(T, TAG, N) \
-    KernelSet<T> kernels_##TAG##_n##N() { SBP_SET_BODY(T, plan_E(N, sizeof(T) == 8), N) }
+#define SBP_DEFINE_SET_N(T, TAG, N)                                                             \
+    KernelSet<T> kernels_##TAG##_n##N() {                                                       \
+        KernelSet<T> s = []() { SBP_SET_BODY(T, plan_E(N, sizeof(T) == 8), N) }();              \
+        s.y_fwd_tma = k_y_tma<T, plan_E(N, sizeof(T) == 8), false, N, ypass_cols(N, sizeof(T) == 8)>; \
+        s.y_inv_tma = k_y_tma<T, plan_E(N, sizeof(T) == 8), true, N, ypass_cols(N, sizeof(T) == 8)>;  \
+        return s;                                                                               \
+    }

@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "sbp_fft.cuh"
+#include "sbp_tma.cuh"
 
 namespace sbp {
 
@@ -390,6 +391,60 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass
     }
     if (valid) {
         cpx<T>* dst = col;
+#pragma unroll
+        for (int e = 0; e < E; ++e, dst += step) *dst = INV ? cconj(v[0][e]) : v[0][e];
+    }
+}
+
+// y pass with a TMA tile load (static lengths): one thread loads the whole
+// [NS][CS] column tile of plane z into shared memory with cp.async.bulk.tensor
+// on an mbarrier, the tile then serves as the FFT's exchange buffer, and the
+// results are stored straight from registers.
+// smem: tile [NS][CS] (128-byte aligned) | tw[NS] | mbarrier
+template <typename T, int E, bool INV, int NS, int CS>
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
+    k_y_tma(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A, TmaCtl ctl,
+            const __grid_constant__ CUtensorMap tmap) {
+    constexpr int Tf = NS / E;
+    constexpr int C = CS;
+    constexpr int BOXR = NS < 256 ? NS : 256;  // rows per TMA box (box dimensions are at most 256)
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* tw = tile + NS * C;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NS);
+    const int tid = threadIdx.x;
+    const int a0 = blockIdx.x * C;
+    const int row0 = blockIdx.y * NS;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0 && !ctl.withhold) {
+        mbar_arrive_expect_tx(bar, (uint32_t)(NS * C * sizeof(cpx<T>)));
+#pragma unroll
+        for (int r = 0; r < NS; r += BOXR) tma_load_2d(tile + r * C, &tmap, 2 * a0, row0 + r, bar);
+    }
+    for (int i = tid; i < NS; i += blockDim.x) tw[i] = twg[i];
+    const bool ok = mbar_wait_bounded(bar, 0, ctl.budget);
+    if (!__syncthreads_and(ok)) {  // uniform exit: the copy did not arrive in time
+        if (tid == 0) atomicExch(ctl.err, 1);
+        return;
+    }
+
+    const int c = tid % C, t = tid / C;
+    const int a = a0 + c;
+    cpx<T> v[1][E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const cpx<T> x = tile[(t + Tf * e) * C + c];
+        v[0][e] = INV ? cconj(x) : x;
+    }
+    const SmemCol<T, C> buf[1] = {{tile + c, 0}};
+    fft_static<NS, E, 0, 1, T>(v, t, tw, buf);  // first exchange write follows a barrier
+    if (a < A.h) {
+        cpx<T>* dst = W + ((size_t)row0 + t) * A.pitch + a;
+        const size_t step = (size_t)Tf * A.pitch;
 #pragma unroll
         for (int e = 0; e < E; ++e, dst += step) *dst = INV ? cconj(v[0][e]) : v[0][e];
     }

@@ -47,6 +47,9 @@ class Stage(IntEnum):
 class Option(IntEnum):
     Z_VARIANT = 1
     XY_PASSES = 2
+    Y_TMA = 3
+    SPIN_BUDGET = 4
+    DEBUG_WITHHOLD_COPY = 5
 
 
 class SbpError(RuntimeError):
@@ -73,6 +76,7 @@ SIGNATURES = {
     "sbp_plan_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_size_t)]),
     "sbp_run_stage": (_c_int, [_vp, _c_int, _vp, _vp, _c_double, _vp]),
+    "sbp_plan_sync_status": (_c_int, [_vp, _vp]),
     "sbp_version": (ctypes.c_char_p, []),
     "sbp_solve_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
                                    _c_double, _vp, _vp, _c_double, _vp]),
@@ -160,6 +164,10 @@ class Plan:
 
     def set_option(self, option, value):
         _check(lib().sbp_plan_set_option(self._h, int(option), float(value)), "sbp_plan_set_option")
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise SbpError if a device-side bounded wait gave up."""
+        _check(lib().sbp_plan_sync_status(self._h, _stream_handle(stream)), "sbp_plan_sync_status")
 
     def new_spectrum(self):
         import torch

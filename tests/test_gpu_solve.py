@@ -229,3 +229,21 @@ def test_box512_fp32_against_fp64_and_oracle_copy(sbp):
     want = O.solve(small, _params(sbox), W.T_512)
     assert rel_l2(_gpu_solve(sbp, sbox, small, W.T_512, 0), want) <= TOL[0]
     assert rel_l2(_gpu_solve(sbp, sbox, small.astype(np.float32), W.T_512, 1), want) <= TOL[1]
+
+
+@pytest.mark.slow
+def test_box1024_clumpy_fp32_against_fp64(sbp):
+    # 1024×1024×512 clumpy disc: FP32 against the FP64 GPU solve (the oracle
+    # cannot do this size); plus linearity of the FP32 solve at full size
+    import torch
+
+    box = W.BOX_1024
+    rho = W.clumpy_disc(box, seed=5, device="cuda", dtype=np.float64)
+    p64 = _plan(sbp, box, 0)
+    ref = p64.solve(rho, t=W.T_1024)
+    p64.close()
+    del p64
+    p32 = _plan(sbp, box, 1)
+    got = p32.solve(rho.float(), t=W.T_1024)
+    err = (torch.linalg.vector_norm((got.double() - ref).ravel()) / torch.linalg.vector_norm(ref.ravel())).item()
+    assert err <= TOL[1], err
