@@ -143,6 +143,14 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
     two_sum(s, e, h, l);
     return {h, l};
 }
+// Compensated (Kahan) running sum: hi holds the sum, lo the negated
+// running error; four float operations per value.
+__device__ __forceinline__ void kahan_add(FF& a, float x) {
+    const float y = x + a.lo;
+    const float t = a.hi + y;
+    a.lo = y - (t - a.hi);
+    a.hi = t;
+}
 __device__ __forceinline__ FF ff_add_f(FF a, float b) {
     float s, e;
     two_sum(a.hi, b, s, e);
@@ -302,8 +310,8 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forw
             FF acc = {0.f, 0.f};
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                acc = ff_add_f(acc, (float)v[0][e].x);
-                acc = ff_add_f(acc, (float)v[0][e].y);
+                kahan_add(acc, (float)v[0][e].x);
+            kahan_add(acc, (float)v[0][e].y);
             }
             // block reduction; the last warp may be partial, so only lanes
             // that exist are added

@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
                 const int x = t + TF * e;
                 v[0][e] = {__ldcs(r0p + x), __ldcs(r0p + N + x)};
                 if constexpr (sizeof(T) == 4) {
-                    acc = ff_add_f(acc, (float)v[0][e].x);
-                    acc = ff_add_f(acc, (float)v[0][e].y);
+                    kahan_add(acc, (float)v[0][e].x);
+                    kahan_add(acc, (float)v[0][e].y);
                 }
             }
             const SmemRow<T> buf[1] = {{xb + c * SH::RP, 0}};
