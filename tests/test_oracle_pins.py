@@ -335,3 +335,37 @@ def test_k0_potential_is_mean_mode():
     mean = np.broadcast_to(rho.mean(axis=(1, 2), keepdims=True), rho.shape).copy()
     v = O.k0_potential(O.plane_sums(rho), 8, 6, 8, p)
     assert np.allclose(O.solve(mean, p, 0.4)[:, 0, 0], v, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("H", [1.0, 3.0])
+def test_paper_alpha_11_fourfold_padding_3d_mode(H):
+    # Sect. 2.3/2.4 parameters (α = 1.1, domain quadrupled in z): same
+    # closed-form error and 2nd-order convergence as α = 1 with 2× padding.
+    L = 6.0
+    kx = 2.0 * np.pi / L
+    n = 8
+    x = A.cell_centres(n, L)
+    horiz = np.cos(kx * x)[None, :] * np.cos(kx * x)[:, None]
+    errs = []
+    ns = [16, 32, 64]
+    for nz in ns:
+        z = A.cell_centres(nz, L)
+        rho = horiz[None] * np.exp(-0.5 * (z / H) ** 2)[:, None, None]
+        ex = 4.0 * np.pi * horiz[None] * A.mode_profile_paper(z, np.sqrt(2.0) * kx, H, L)[:, None, None]
+        e4 = A.rel_l2(O.solve(rho, O.SolveParams(L, L, L, pad=4, alpha=1.1), 0.0), ex)
+        e2 = A.rel_l2(O.solve(rho, O.SolveParams(L, L, L), 0.0), ex)
+        assert abs(e4 - e2) < 0.05 * e2
+        errs.append(e4)
+    assert 1.85 < _fit_order(ns, errs) < 2.15
+
+
+def test_alpha_11_needs_fourfold_padding():
+    # R1: with 2× padding the α = 1.1 kernel aliases the k = 0 column's image
+    # at ±2Lz; the centred 1D Gaussian then stalls near 5e-3 instead of converging.
+    L = 6.0
+    z = A.cell_centres(64, L)
+    rho = np.broadcast_to(np.exp(-0.5 * z ** 2)[:, None, None], (64, 4, 4)).copy()
+    ex = A.gauss1d_potential_exact(z, 0.0, L)
+    bad = A.rel_l2(O.solve(rho, O.SolveParams(L, L, L, pad=2, alpha=1.1), 0.0)[:, 0, 0], ex)
+    good = A.rel_l2(O.solve(rho, O.SolveParams(L, L, L, pad=4, alpha=1.1), 0.0)[:, 0, 0], ex)
+    assert bad > 1e-3 and good < 2e-5
