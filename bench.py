@@ -371,9 +371,13 @@ def main():
         from paper_2510_10070_gb300 import workloads as W
 
         rho256 = W.lognormal_disc(W.BOX_256, seed=2, sigma=0.5)
-        for name, d in (("box256_fp64", 0), ("box256_fp32", 1)):
+        # alpha = 1.1 with 4·nz padding: the paper's own vertical truncation (Sect. 2.3)
+        for name, d, alpha in (("box256_fp64", 0, 1.0), ("box256_fp32", 1, 1.0),
+                               ("box256_fp64_alpha1.1_pad4", 0, 1.1), ("box256_fp32_alpha1.1_pad4", 1, 1.1)):
             b = W.BOX_256
             p = sbp.Plan(b.nx, b.ny, b.nz, b.Lx, b.Ly, b.Lz, q=b.q, dtype=d)
+            if alpha != 1.0:
+                p.set_option(sbp.Option.TRUNCATION, alpha)
             r = torch.from_numpy(rho256).to(device=dev, dtype=torch.float64 if d == 0 else torch.float32)
             f = torch.empty_like(r)
             for _ in range(3):

@@ -156,12 +156,24 @@ enum {
     /* Test switch: 1 makes the TMA kernels arm no copy, so that their bounded
      * waits run out (the results are then undefined and
      * sbp_plan_sync_status reports SBP_ERR_DEVICE_TIMEOUT); 0 restores. */
-    SBP_OPT_DEBUG_WITHHOLD_COPY = 5
+    SBP_OPT_DEBUG_WITHHOLD_COPY = 5,
+    /* Vertical truncation length L = alpha·Lz of the Green's function
+     * (Sect. 2.3: the regularized kernel of Eq. (Green's function regularized
+     * in Fourier) with L ≥ Lz; the paper takes alpha = 1.1 and pads the
+     * vertical transform to 4·nz).  1 (default): L = Lz with 2·nz padding;
+     * 1 < alpha ≤ 3: L = alpha·Lz with 4·nz padding (one length-4nz transform
+     * per column; the periodic images then stay outside |z| < Lz).  Fourfold
+     * padding is built for power-of-two nz from 32 to 512 (FP32) or 256
+     * (FP64); other nz return SBP_ERR_UNSUPPORTED_SIZE and keep the old
+     * setting.  SBP_OPT_Z_VARIANT then accepts only 0. */
+    SBP_OPT_TRUNCATION = 6
 };
 
 /* sbp_plan_set_option — set a plan option (see the enum above).  Unknown
  * options or values return SBP_ERR_INVALID_ARG.  Not to be called while a
- * solve of this plan is in flight. */
+ * solve of this plan is in flight.  Options that change kernels (Z_VARIANT,
+ * XY_PASSES, Y_TMA, TRUNCATION) synchronise the device and drop the cached
+ * sbp_solve_batched graphs that contain this plan. */
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value);
 
 /* sbp_plan_sync_status — synchronise `stream` and report device-side

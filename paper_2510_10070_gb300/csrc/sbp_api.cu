@@ -91,6 +91,10 @@ struct sbp_plan_s {
     PassCfg xf, xi, yp, zp;
     int z_variant = 0;         // see SBP_OPT_Z_VARIANT
     bool z_padded = false;     // the chosen kernel takes the length-2nz twiddle table
+    // vertical truncation L = alpha·Lz (SBP_OPT_TRUNCATION); alpha > 1 pads
+    // the vertical transform to pad = 4 times nz (else 2)
+    double alpha = 1.0;
+    int pad = 2;
     void* z_fn = nullptr;      // the z-pass kernel of the chosen variant
     int green_blocks = 0;      // x-forward blocks that fill the Green's table
     // fused xy plane kernels (square planes with a built kernel), used by solves
@@ -108,6 +112,8 @@ struct sbp_plan_s {
     void* tw_z = nullptr;
     void* tw_2z = nullptr;
     void* tw_M = nullptr;      // e^{-2πi k/(2nz)}, k < 2nz
+    void* tw_M4 = nullptr;     // e^{-2πi k/(4nz)}, k < 4nz
+    void* paper_tab = nullptr; // per |m| ≤ 2nz: k_z sin(k_z L), 1 - cos(k_z L), k_z², Ĝ(0, k_z) (pad = 4)
     void* kz2 = nullptr;
     double* c00 = nullptr;
     double* tile_sums = nullptr;
@@ -139,6 +145,15 @@ size_t zpad_smem(int n, int C) {
     const size_t cs = sizeof(cpx<T>);
     const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
     return 2 * (size_t)n * cs + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
+}
+
+// k_z_paper: twM[4n] | table [2n+1][4] | green[C] | skewed exchange of C columns of 4n
+template <typename T>
+size_t zpaper_smem(int n, int C) {
+    const size_t cs = sizeof(cpx<T>);
+    const size_t tab_bytes = align_up(4 * (size_t)(2 * n + 1) * sizeof(T), 16);
+    const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
+    return 4 * (size_t)n * cs + tab_bytes + gm_bytes + (size_t)skew_slots(4 * n, C) * cs;
 }
 
 template <typename T>
@@ -220,6 +235,32 @@ template <typename T>
 bool configure_z(sbp_plan_s* p, int variant) {
     const bool f64 = std::is_same<T, double>::value;
     const int cmax = f64 ? 8 : 16;
+    if (p->pad == 4) {
+        // fourfold padding has one kernel: k_z_paper (power-of-two nz ≤ 512 FP32, ≤ 256 FP64)
+        if (variant != 0) return false;
+        int E = 0;
+        ZKernel<T> fn = zpaper_for<T>(p->nz, &E);
+        if (!fn) return false;
+        FftPlan P;
+        if (!build_fft_plan(4 * p->nz, E, P)) return false;
+        const int C = zpad_cols(2 * p->nz, E, f64);
+        const size_t smem = zpaper_smem<T>(p->nz, C);
+        if (C * P.Tf > kMaxThreads || smem > kSmemBudget) return false;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        p->pz = P;
+        p->zp.E = E;
+        p->zp.C = C;
+        p->zp.threads = C * P.Tf;
+        p->zp.smem = smem;
+        p->zp.grid = dim3((unsigned)((p->h + C - 1) / C), (unsigned)p->ny, 1);
+        p->z_variant = 0;
+        p->z_padded = false;
+        p->z_fn = reinterpret_cast<void*>(fn);
+        return true;
+    }
     if (variant == 0) return configure_z<T>(p, 3) || configure_z<T>(p, 4);
     int E = plan_E(p->nz, f64);
     bool joint = false, padded = false;
@@ -362,21 +403,51 @@ void host_twiddles(std::vector<double>& out, int count, double frac_den) {
     }
 }
 
-// k = 0 vertical kernel with L = Lz, M = 2nz (Eq. Green's function regularized
-// in Fourier, first two cases, with k_z L = π m):  Ĝ(0,0) = Lz²/2,
-// Ĝ(0, m) = ((-1)^m - 1)/k_z²;  c00_n = (1/M) Σ_m Ĝ(0, m) cos(π m n / nz).
-void host_c00(std::vector<double>& c, int nz, double Lz) {
-    const int M = 2 * nz;
+// k = 0 vertical kernel (Eq. Green's function regularized in Fourier, first
+// two cases): Ĝ(0,0) = L²/2, Ĝ(0, k_z) = [k_z L sin(k_z L) + cos(k_z L) - 1]/k_z²
+// at k_z = 2π m/(pad·Lz), m ∈ [-pad·nz/2, pad·nz/2).
+double g0_vertical(double kz, double L) {
+    if (kz == 0.0) return 0.5 * L * L;
+    const double a = kz * L;
+    return (a * std::sin(a) + std::cos(a) - 1.0) / (kz * kz);
+}
+
+// c00_n = (1/M) Σ_m Ĝ(0, m) cos(2π m n / M) for |n| < nz, M = pad·nz.  With
+// L = Lz and pad = 2 (k_z L = π m) the terms are ((-1)^m - 1)/k_z²; the
+// integer phase m·n mod M keeps the cosines exact to rounding.
+void host_c00(std::vector<double>& c, int nz, double Lz, int pad, double L) {
+    const int M = pad * nz;
     c.assign(2 * (size_t)nz - 1, 0.0);
+    std::vector<double> g(M);
+    const bool exact = (pad == 2 && L == Lz);
+    for (int m = -M / 2; m < M / 2; ++m) {
+        const double kz = kTwoPi * (double)m / (pad * Lz);
+        g[m + M / 2] = !exact ? g0_vertical(kz, L) : (m == 0 ? 0.5 * L * L : ((m & 1) ? -2.0 / (kz * kz) : 0.0));
+    }
     for (int n = -(nz - 1); n <= nz - 1; ++n) {
-        double acc = 0.5 * Lz * Lz;
-        for (int m = -nz; m < nz; ++m) {
-            if ((m & 1) == 0) continue;  // even m ≠ 0 contribute zero
-            const double kz = M_PI * (double)m / Lz;
-            const long long ph = ((long long)m * n) % M;
-            acc += (-2.0 / (kz * kz)) * std::cos(M_PI * (double)ph / (double)nz);
+        double acc = 0.0;
+        for (int m = -M / 2; m < M / 2; ++m) {
+            long long ph = ((long long)m * n) % M;
+            if (ph < 0) ph += M;
+            acc += g[m + M / 2] * std::cos(kTwoPi * (double)ph / (double)M);
         }
         c[n + nz - 1] = acc / (double)M;
+    }
+}
+
+// Per |m| ≤ 2nz for fourfold padding: k_z sin(k_z L), 1 - cos(k_z L) (as
+// 2 sin²(k_z L/2)), k_z² and Ĝ(0, k_z), with k_z = π m/(2 Lz), L = alpha·Lz,
+// laid out [m][4] so that one m is one 16-byte (FP32) load.
+void host_paper_tab(std::vector<double>& out, int nz, double Lz, double L) {
+    const int NT = 2 * nz + 1;
+    out.assign(4 * (size_t)NT, 0.0);
+    for (int m = 0; m < NT; ++m) {
+        const double kz = kTwoPi * (double)m / (4.0 * Lz);
+        const double h = std::sin(0.5 * kz * L);
+        out[4 * m] = kz * std::sin(kz * L);
+        out[4 * m + 1] = 2.0 * h * h;
+        out[4 * m + 2] = kz * kz;
+        out[4 * m + 3] = g0_vertical(kz, L);
     }
 }
 
@@ -396,7 +467,10 @@ sbp_status upload_tables(sbp_plan_s* p) {
     }
     const bool f32 = !f64_of(p);
     std::vector<double> c00;
-    if (f32) host_c00(c00, p->nz, p->Lz);
+    if (f32) host_c00(c00, p->nz, p->Lz, p->pad, p->alpha * p->Lz);
+    std::vector<double> twM4, ptab;
+    host_twiddles(twM4, 4 * p->nz, 4.0 * p->nz);  // e^{-2πi k/(4nz)}
+    host_paper_tab(ptab, p->nz, p->Lz, p->alpha * p->Lz);
 
     const size_t cs = sizeof(cpx<T>);
     const int tiles = (int)p->xf.grid.x;
@@ -409,6 +483,8 @@ sbp_status upload_tables(sbp_plan_s* p) {
     const size_t o_twx = take(p->nx * cs), o_twy = take(p->ny * cs), o_twz = take(p->nz * cs);
     const size_t o_tw2 = take(p->nz * cs), o_kz2 = take((p->nz + 1) * sizeof(T));
     const size_t o_twM = take(2 * (size_t)p->nz * cs);
+    const size_t o_twM4 = take(4 * (size_t)p->nz * cs);
+    const size_t o_ptab = take(ptab.size() * sizeof(T));
     const size_t o_c00 = take((2 * (size_t)p->nz) * sizeof(double));
     const size_t o_ts = take((size_t)tiles * sizeof(double));
     const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
@@ -430,6 +506,8 @@ sbp_status upload_tables(sbp_plan_s* p) {
     p->vk0 = reinterpret_cast<double*>(base + o_vk0);
     p->err = reinterpret_cast<int*>(base + o_err);
     p->tw_M = base + o_twM;
+    p->tw_M4 = base + o_twM4;
+    p->paper_tab = base + o_ptab;
     p->green = base + o_green;
 
     std::vector<unsigned char> host(off, 0);
@@ -442,6 +520,8 @@ sbp_status upload_tables(sbp_plan_s* p) {
     put_cpx(o_twz, twz);
     put_cpx(o_tw2, tw2);
     put_cpx(o_twM, twM);
+    put_cpx(o_twM4, twM4);
+    put_cpx(o_ptab, ptab);  // real table: same element-wise conversion
     {
         T* d = reinterpret_cast<T*>(host.data() + o_kz2);
         for (int m = 0; m <= p->nz; ++m) d[m] = (T)kz2[m];
@@ -450,6 +530,28 @@ sbp_status upload_tables(sbp_plan_s* p) {
     if (cudaMemcpy(p->tables, host.data(), off, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         return SBP_ERR_CUDA;
+    }
+    return SBP_OK;
+}
+
+// Re-derive the tables that depend on the vertical truncation (FP32 c00 and
+// the fourfold-padding table) after alpha or pad changed.
+template <typename T>
+sbp_status refresh_vertical_tables(sbp_plan_s* p) {
+    std::vector<double> ptab;
+    host_paper_tab(ptab, p->nz, p->Lz, p->alpha * p->Lz);
+    std::vector<T> pt(ptab.begin(), ptab.end());
+    if (cudaMemcpy(p->paper_tab, pt.data(), pt.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    if (!f64_of(p)) {
+        std::vector<double> c00;
+        host_c00(c00, p->nz, p->Lz, p->pad, p->alpha * p->Lz);
+        if (cudaMemcpy(p->c00, c00.data(), c00.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return SBP_ERR_CUDA;
+        }
     }
     return SBP_OK;
 }
@@ -494,7 +596,7 @@ GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
     g.ny = p->ny;
     g.Lx = p->Lx;
     g.Ly = p->Ly;
-    g.L = p->Lz;
+    g.L = p->alpha * p->Lz;
     g.s = shear_s(p, t);
     g.s_dev = nullptr;
     return g;
@@ -538,9 +640,10 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     a.h = p->h;
     a.ny = p->ny;
     a.C = p->zp.C;
-    a.L = p->Lz;
+    a.L = p->alpha * p->Lz;
     a.kzc = (M_PI / p->Lz) * (M_PI / p->Lz);
-    a.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * 2.0 * p->nz);
+    a.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * (double)p->pad * p->nz);
+    a.paper_tab = p->paper_tab;
     const bool f32 = !f64_of(p);
     a.zero_k0 = f32 ? 1 : 0;
     a.green = p->green;
@@ -601,7 +704,7 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
         case SBP_STAGE_Z_CONVOLVE:
             reinterpret_cast<ZKernel<T>>(p->z_fn)<<<p->zp.grid, p->zp.threads, p->zp.smem, st>>>(
                 W, static_cast<const cpx<T>*>(p->tw_z),
-                static_cast<const cpx<T>*>(p->z_padded ? p->tw_M : p->tw_2z),
+                static_cast<const cpx<T>*>(p->pad == 4 ? p->tw_M4 : (p->z_padded ? p->tw_M : p->tw_2z)),
                 static_cast<const T*>(p->kz2), make_zargs<T>(p, fused));
             break;
         case SBP_STAGE_Y_INVERSE:
@@ -746,6 +849,22 @@ void free_exec(BatchExec* e) {
     delete e;
 }
 
+// Batched executors that reference plan p (their graphs hold its launch
+// configuration): freed when the plan is destroyed or reconfigured.  The
+// caller has synchronised the device.
+void drop_executors(const sbp_plan_s* p) {
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    for (size_t i = 0; i < g_execs.size();) {
+        BatchExec* e = g_execs[i];
+        if (std::find(e->plans.begin(), e->plans.end(), p) != e->plans.end()) {
+            free_exec(e);
+            g_execs.erase(g_execs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 sbp_status capture_batch(BatchExec* e, int K, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
     const int n = (int)e->plans.size();
     cudaStream_t cap = nullptr;
@@ -862,6 +981,23 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
     return SBP_OK;
+}
+
+template <typename T>
+sbp_status set_truncation(sbp_plan_s* p, double alpha) {
+    const double old_alpha = p->alpha;
+    const int old_pad = p->pad;
+    p->alpha = alpha;
+    p->pad = (alpha == 1.0) ? 2 : 4;
+    sbp_status st = refresh_vertical_tables<T>(p);
+    if (st == SBP_OK && !configure_z<T>(p, 0)) st = SBP_ERR_UNSUPPORTED_SIZE;
+    if (st != SBP_OK) {
+        p->alpha = old_alpha;
+        p->pad = old_pad;
+        refresh_vertical_tables<T>(p);
+        configure_z<T>(p, p->z_variant);
+    }
+    return st;
 }
 
 }  // namespace
@@ -1015,19 +1151,7 @@ void sbp_plan_destroy(sbp_plan p) {
         DeviceGuard g(p->device);
         cudaDeviceSynchronize();
         cudaGetLastError();
-        {
-            // batched executors that reference this plan go with it
-            std::lock_guard<std::mutex> lock(g_exec_mu);
-            for (size_t i = 0; i < g_execs.size();) {
-                BatchExec* e = g_execs[i];
-                if (std::find(e->plans.begin(), e->plans.end(), p) != e->plans.end()) {
-                    free_exec(e);
-                    g_execs.erase(g_execs.begin() + i);
-                } else {
-                    ++i;
-                }
-            }
-        }
+        drop_executors(p);
         free_plan(p);
     }
 }
@@ -1049,6 +1173,21 @@ const char* sbp_status_string(sbp_status s) {
 
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
+    if (option == SBP_OPT_Y_TMA || option == SBP_OPT_XY_PASSES || option == SBP_OPT_Z_VARIANT ||
+        option == SBP_OPT_TRUNCATION) {
+        // captured batch graphs hold the old kernels and arguments
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        drop_executors(p);
+    }
+    if (option == SBP_OPT_TRUNCATION) {
+        if (!(value == 1.0 || (value > 1.0 && value <= 3.0))) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        return f64_of(p) ? set_truncation<double>(p, value) : set_truncation<float>(p, value);
+    }
     if (option == SBP_OPT_Y_TMA) {
         if (value != 0.0 && value != 1.0) return SBP_ERR_INVALID_ARG;
         DeviceGuard g(p->device);
@@ -1078,6 +1217,7 @@ sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (option == SBP_OPT_Z_VARIANT) {
         const int v = (int)value;
         if ((double)v != value || v < 0 || v > 4) return SBP_ERR_INVALID_ARG;
+        if (p->pad == 4 && v != 0) return SBP_ERR_UNSUPPORTED_SIZE;  // one kernel for fourfold padding
         DeviceGuard g(p->device);
         if (!g.ok) return SBP_ERR_CUDA;
         const bool ok = f64_of(p) ? configure_z<double>(p, v) : configure_z<float>(p, v);

@@ -273,6 +273,40 @@ struct DftHalf<12, T> {
     static __device__ __forceinline__ void run(cpx<T>* x) { dft_split_half<4, 3, T>(x); }
 };
 
+// DFTs whose inputs beyond the first quarter are zero (x[R/4 ..] == 0), for
+// the first stage of a transform zero-padded to four times its data.
+template <int R, typename T>
+struct DftQuarter;
+
+template <typename T>
+struct DftQuarter<8, T> {  // X_k = x0 + x1·ω8^k
+    static __device__ __forceinline__ void run(cpx<T>* x) {
+        const cpx<T> a = x[0], b = x[1];
+        static_for<0, 8>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            x[k] = cadd(a, twiddle_const<8, k>(b));
+        });
+    }
+};
+
+template <typename T>
+struct DftQuarter<16, T> {  // n = 4·n1 + n2 with n1 = 0: X[k1 + 4k2] = Σ_{n2<4} ω16^{n2·k1} ω4^{n2·k2} x[n2]
+    static __device__ __forceinline__ void run(cpx<T>* x) {
+        cpx<T> in[4] = {x[0], x[1], x[2], x[3]};
+        static_for<0, 4>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            cpx<T> b[4];
+            static_for<0, 4>([&](auto n2c) {
+                constexpr int n2 = decltype(n2c)::value;
+                b[n2] = twiddle_const<16, n2 * k1>(in[n2]);
+            });
+            Dft<4, T>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = b[k2];
+        });
+    }
+};
+
 template <typename T>
 struct Dft<6, T> {
     static __device__ __forceinline__ void run(cpx<T>* x) { dft_split<3, 2, T>(x); }
@@ -327,6 +361,19 @@ struct SmemCol {
 };
 template <typename T>
 using SmemRow = SmemCol<T, 0>;
+
+// C interleaved columns with a skewed element index: element i of column c
+// sits at base_c[C·(i + i/16)].  Lanes of a warp run over (c, t) with c
+// fastest; with 4 t per warp (8-byte elements, C = 8) the skew splits every
+// exchange access (stride-1 or stride-16 in t) evenly over the banks, so it
+// takes the minimum two wavefronts.
+template <typename T, int C>
+struct SmemColSkew {
+    cpx<T>* base;
+    __device__ __forceinline__ cpx<T>& operator[](int i) const { return base[C * (i + (i >> 4))]; }
+};
+// Complex slots of a skewed exchange buffer of C columns of n elements.
+__host__ __device__ constexpr int skew_slots(int n, int C) { return C * (n + (n >> 4)); }
 // Complex slots of one row-layout buffer of n elements.
 __host__ __device__ constexpr int padded_row(int n) { return n + (n >> 4) + 1; }
 
@@ -546,6 +593,34 @@ __device__ __forceinline__ void fft_static_padded(cpx<T> (&v)[NCOL][E], int t, c
 #pragma unroll
         for (int r = 0; r < E / 2; ++r) x[r] = v[c][r];
         DftHalf<E, T>::run(x);
+#pragma unroll
+        for (int r = 0; r < E; ++r) buf[c][t * E + r] = x[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[c][e] = buf[c][t + TF * e];
+    }
+    fft_static<M, E, 1, NCOL, T, BUF>(v, t, tw, buf);
+}
+
+// Forward length-M transform of data whose last three quarters are zero:
+// v[e] = x[t + Tf·e] with v[e] = 0 for e ≥ E/4 (never read).
+template <int M, int E, int NCOL, typename T, typename BUF>
+__device__ __forceinline__ void fft_static_quarter(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ tw,
+                                                   const BUF (&buf)[NCOL]) {
+    constexpr int NST = static_nstage(M, E);
+    static_assert(static_radix(M, E, 0) == E, "pruned first stage needs one butterfly per thread");
+    static_assert(NST >= 2, "padded transform needs at least two stages");
+    constexpr int TF = M / E;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        cpx<T> x[E];
+#pragma unroll
+        for (int r = 0; r < E / 4; ++r) x[r] = v[c][r];
+        DftQuarter<E, T>::run(x);
 #pragma unroll
         for (int r = 0; r < E; ++r) buf[c][t * E + r] = x[r];
     }

@@ -69,6 +69,27 @@ SBP_ZPAD_LIST(SBP_DECLARE_ZPAD)
 #define SBP_DEFINE_ZPAD(T, TAG, N, E) \
     ZKernel<T> zpad_##TAG##_n##N() { return k_z_padded<T, E, N>; }
 
+// Paper-parameter z variant (α ≠ 1, 4× padding): (type, N, E).
+#define SBP_ZPAPER_LIST(X) X(float, f32, 32, 16) X(float, f32, 64, 16) X(float, f32, 128, 16) \
+    X(float, f32, 256, 16) X(float, f32, 512, 16) X(double, f64, 32, 8) X(double, f64, 64, 8) X(double, f64, 128, 8) \
+    X(double, f64, 256, 8)
+#define SBP_DECLARE_ZPAPER(T, TAG, N, E) ZKernel<T> zpaper_##TAG##_n##N();
+SBP_ZPAPER_LIST(SBP_DECLARE_ZPAPER)
+#define SBP_DEFINE_ZPAPER(T, TAG, N, E) \
+    ZKernel<T> zpaper_##TAG##_n##N() { return k_z_paper<T, E, N>; }
+
+template <typename T>
+inline ZKernel<T> zpaper_for(int n, int* E_out) {
+#define SBP_MATCH_ZPAPER(TT, TAG, N, EE)                                 \
+    if (std::is_same<T, TT>::value && n == N) {                          \
+        *E_out = EE;                                                     \
+        return reinterpret_cast<ZKernel<T>>(zpaper_##TAG##_n##N());      \
+    }
+    SBP_ZPAPER_LIST(SBP_MATCH_ZPAPER)
+#undef SBP_MATCH_ZPAPER
+    return nullptr;
+}
+
 // Padded z kernel for length n and its elements per thread (null if not built).
 template <typename T>
 inline ZKernel<T> zpad_for(int n, int* E_out) {

@@ -91,6 +91,9 @@ struct ZArgs {
     const double* c00;
     double k0_coef;
     double* vk0;
+    // α ≠ 1 with 4·nz padding (the paper's Sect. 2.3 parameters): per |m| ≤ 2nz
+    // k_z sin(k_z L), 1 - cos(k_z L), k_z² and Ĝ(0, k_z), [m][4] in the plan's type
+    const void* paper_tab;
 };
 
 // Block (0,0) of a z pass: the FP64 mean mode (O(nz²) FP64 work on one SM,
@@ -105,6 +108,7 @@ __device__ __forceinline__ void mean_mode_fp64(const ZArgs& A, int nz, double* s
     __syncthreads();
     for (int i = tid; i < nz; i += blockDim.x) {
         double acc = 0.0;
+#pragma unroll 4
         for (int j = 0; j < nz; ++j) acc = fma(A.c00[i - j + nz - 1], scratch[j], acc);
         A.vk0[i] = A.k0_coef * acc;
     }
@@ -745,6 +749,112 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padde
         cpx<T>* dst = col;
 #pragma unroll
         for (int e = 0; e < E / 2; ++e, dst += step) *dst = cconj(v[0][e]);
+    }
+}
+
+// Paper-parameter variant (α = L/Lz ≠ 1, padding M = 4N): one length-4N
+// transform per column, first stage pruned to the nonzero quarter, and the
+// general three-case Ĝ of Eq. (Green's function regularized in Fourier):
+//   k ≠ 0: -[e^{-kL}((k_z/k) sin(k_z L) - cos(k_z L)) + 1]/(k² + k_z²)
+//        = -[e^{-kL}((k_z/k) sin(k_z L) + (1 - cos k_z L)) + (1 - e^{-kL})]/(k² + k_z²)
+//   k = 0: table value (L²/2 at k_z = 0)
+// The second form adds no cancellation of its own in FP32: 1 - e^{-kL} comes
+// from expm1 and 1 - cos(k_z L) from the FP64 host tables.
+// smem: twM[M] | table [2N+1][4] | green[C] | skewed exchange of C columns
+template <typename T, int E, int N>
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_paper(
+    cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/, const cpx<T>* __restrict__ twMg,
+    const T* __restrict__ /*unused*/, ZArgs A) {
+    constexpr int M = 4 * N;
+    constexpr int Tf = M / E;
+    constexpr int C = zpad_cols(2 * N, E, sizeof(T) == 8);  // same rule with 2·(2N) per column
+    constexpr int NT = 2 * N + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* twM = reinterpret_cast<cpx<T>*>(smem_raw);
+    T* tab = reinterpret_cast<T*>(twM + M);  // per |m|: k_z sin(k_z L), 1 - cos(k_z L), k_z², Ĝ(0, k_z)
+    constexpr int tab_bytes = (4 * NT * (int)sizeof(T) + 15) / 16 * 16;
+    GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(reinterpret_cast<unsigned char*>(tab) + tab_bytes);
+    constexpr int gm_bytes = ((C * (int)sizeof(GreenT<T>)) + 15) / 16 * 16;
+    cpx<T>* xb = reinterpret_cast<cpx<T>*>(reinterpret_cast<unsigned char*>(gm) + gm_bytes);
+
+    const int tid = threadIdx.x;
+    for (int i = tid; i < M; i += blockDim.x) twM[i] = twMg[i];
+    const T* ptab = static_cast<const T*>(A.paper_tab);
+    for (int i = tid; i < 4 * NT; i += blockDim.x) tab[i] = ptab[i];
+    const int b = blockIdx.y;
+    if (tid < C) {
+        const int a = blockIdx.x * C + tid;
+        GreenT<T> g = {};
+        g.kzero = 1;  // columns past the half spectrum: finite, never stored
+        g.same = 1;
+        if (a < A.h) g = static_cast<const GreenT<T>*>(A.green)[(size_t)b * A.h + a];
+        gm[tid] = g;
+    }
+    if (A.vk0 != nullptr && blockIdx.x == 0 && blockIdx.y == 0)
+        mean_mode_fp64(A, N, reinterpret_cast<double*>(xb));
+
+    const int c = tid % C, t = tid / C;
+    const int a = blockIdx.x * C + c;
+    const bool valid = a < A.h;
+    const size_t zstride = (size_t)A.ny * A.pitch;
+    const size_t step = (size_t)Tf * zstride;
+    cpx<T>* col = W + (size_t)b * A.pitch + a + (size_t)t * zstride;
+    cpx<T> v[1][E];
+    {
+        const cpx<T>* src = col;
+#pragma unroll
+        for (int e = 0; e < E / 4; ++e, src += step) {
+            cpx<T> x = {(T)0, (T)0};
+            if (valid) x = *src;
+            v[0][e] = x;
+        }
+    }
+    const SmemColSkew<T, C> buf[1] = {{xb + c}};
+    fft_static_quarter<M, E, 1, T>(v, t, twM, buf);  // starts with a barrier: tables are visible
+
+    {
+        const GreenT<T> g = gm[c];
+        const T scale = (T)A.scale;
+        // numerator = A1·(k_z sin k_z L) + A2·(1 - cos k_z L) + A3 per branch
+        const T Ea = (T)1 - g.omEa, Eb = (T)1 - g.omEb;  // e^{-kL}
+        const T ika = g.kzero ? (T)0 : rsqrt(g.k2a);
+        const T ikb = g.kzero ? (T)0 : rsqrt(g.k2b);
+        const T wb = g.same ? (T)0 : (T)0.5, wa = (T)1 - wb;
+        const T a1 = -scale * wa * Ea * ika, a2 = -scale * wa * Ea, a3 = -scale * wa * g.omEa;
+        const T b1 = -scale * wb * Eb * ikb, b2 = -scale * wb * Eb, b3 = -scale * wb * g.omEb;
+        const bool kill = A.zero_k0 && g.kzero;
+        // warp-uniform fast path: every lane's mode is its own partner and k ≠ 0
+        if (__all_sync(0xffffffffu, g.same && !g.kzero)) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int m = t + Tf * e;
+                const int ms = (m <= 2 * N) ? m : M - m;  // |signed m|
+                const T* q = tab + 4 * ms;
+                const T f = fast_div(fma(a1, q[0], fma(a2, q[1], a3)), g.k2a + q[2]);
+                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int m = t + Tf * e;
+                const int ms = (m <= 2 * N) ? m : M - m;
+                const T* q = tab + 4 * ms;
+                T f;
+                if (g.kzero) {
+                    f = kill ? (T)0 : scale * q[3];
+                } else {
+                    f = fast_div(fma(a1, q[0], fma(a2, q[1], a3)), g.k2a + q[2]) +
+                        fast_div(fma(b1, q[0], fma(b2, q[1], b3)), g.k2b + q[2]);
+                }
+                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            }
+        }
+    }
+    fft_static<M, E, 0, 1, T>(v, t, twM, buf);
+    if (valid) {
+        cpx<T>* dst = col;
+#pragma unroll
+        for (int e = 0; e < E / 4; ++e, dst += step) *dst = cconj(v[0][e]);
     }
 }
 

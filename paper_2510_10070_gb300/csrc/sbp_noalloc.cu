@@ -251,6 +251,7 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     za.ny = ny;
     za.C = Cz;
     za.L = Lz;
+    za.paper_tab = nullptr;
     za.kzc = (M_PI / Lz) * (M_PI / Lz);
     za.scale = 4.0 * M_PI * G / ((double)nx * ny * 2.0 * nz);
     za.zero_k0 = 1;

@@ -24,6 +24,7 @@ def main(argv=None):
     ap.add_argument("--t", type=float, default=1.3)
     ap.add_argument("--z-variant", type=int, default=0)
     ap.add_argument("--xy-passes", type=int, default=0)
+    ap.add_argument("--alpha", type=float, default=1.0, help="vertical truncation L/Lz (> 1: 4·nz padding)")
     args = ap.parse_args(argv)
     nx, ny, nz = (int(v) for v in args.box.lower().split("x"))
     Lx, Ly, Lz = (float(v) for v in args.lengths.split(","))
@@ -33,6 +34,8 @@ def main(argv=None):
         plan.set_option(sbp.Option.Z_VARIANT, args.z_variant)
     if args.xy_passes:
         plan.set_option(sbp.Option.XY_PASSES, args.xy_passes)
+    if args.alpha != 1.0:
+        plan.set_option(sbp.Option.TRUNCATION, args.alpha)
     g = torch.Generator(device="cuda").manual_seed(1)
     z = (torch.arange(nz, device="cuda", dtype=torch.float64) + 0.5) * (Lz / nz) - 0.5 * Lz
     rho = torch.exp(-0.5 * z * z)[:, None, None] * (1.0 + 0.1 * torch.rand((nz, ny, nx), generator=g,

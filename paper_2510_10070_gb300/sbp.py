@@ -50,6 +50,7 @@ class Option(IntEnum):
     Y_TMA = 3
     SPIN_BUDGET = 4
     DEBUG_WITHHOLD_COPY = 5
+    TRUNCATION = 6
 
 
 class SbpError(RuntimeError):
