@@ -144,21 +144,23 @@ template <typename T>
 size_t zpad_smem(int n, int C) {
     const size_t cs = sizeof(cpx<T>);
     const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
-    return 2 * (size_t)n * cs + gm_bytes + 2 * (size_t)n * xstride(C) * cs;
+    return 2 * (size_t)n * cs + gm_bytes + (size_t)xchg_slots<T>(2 * n, C) * cs;
 }
 
-// k_z_paper: twM[4n] | table [2n+1][4] | green[C] | skewed exchange of C columns of 4n
+// k_z_paper: twM[4n] | table [2n+1][4] | green[C] | exchange of C columns of 4n
 template <typename T>
 size_t zpaper_smem(int n, int C) {
     const size_t cs = sizeof(cpx<T>);
     const size_t tab_bytes = align_up(4 * (size_t)(2 * n + 1) * sizeof(T), 16);
     const size_t gm_bytes = align_up((size_t)C * sizeof(GreenT<T>), 16);
-    return 4 * (size_t)n * cs + tab_bytes + gm_bytes + (size_t)skew_slots(4 * n, C) * cs;
+    return 4 * (size_t)n * cs + tab_bytes + gm_bytes + (size_t)xchg_slots<T>(4 * n, C) * cs;
 }
 
 template <typename T>
 size_t ypass_smem(int n, int C) {
-    return (size_t)n * sizeof(cpx<T>) + (size_t)n * xstride(C) * sizeof(cpx<T>);
+    // static column counts use XchgCol, runtime ones the padded stride
+    const size_t slots = std::max((size_t)n * xstride(C), (size_t)xchg_slots<T>(n, C));
+    return (size_t)n * sizeof(cpx<T>) + slots * sizeof(cpx<T>);
 }
 
 template <typename T>
@@ -211,7 +213,7 @@ bool configure_ytma(sbp_plan_s* p, bool enable) {
     auto enc = tensor_map_encoder();
     if (!ky.y_fwd_tma || !ky.y_inv_tma || !enc) return false;
     const int C = p->yp.C;
-    const size_t smem = align_up((size_t)p->ny * C * sizeof(cpx<T>), 16) + (size_t)p->ny * sizeof(cpx<T>) + 16;
+    const size_t smem = align_up((size_t)tile_slots<T>(p->ny, C) * sizeof(cpx<T>), 16) + (size_t)p->ny * sizeof(cpx<T>) + 16;
     if (smem > kSmemBudget || (2 * C * sizeof(T)) % 16 != 0) return false;
     if (!encode_ymap<T>(p, p->W, &p->tmap_y)) return false;
     if (cudaFuncSetAttribute(ky.y_fwd_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) !=

@@ -189,6 +189,58 @@ __device__ __forceinline__ void dft_split(cpx<T>* x) {
     }
 }
 
+// Twiddled DFT: X = DFT_R(x[r]·w(r)) with w(0) = 1.  The split radices apply
+// each first-level group's R1 twiddles just before its DFT_R1, so only R1
+// twiddles are live at a time instead of R - 1.
+template <int R1, int R2, typename T, typename TW>
+__device__ __forceinline__ void dft_split_tw(cpx<T>* x, const TW& w) {
+    constexpr int R = R1 * R2;
+    cpx<T> y[R];
+    static_for<0, R2>([&](auto n2c) {
+        constexpr int n2 = decltype(n2c)::value;
+        cpx<T> a[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) {
+            const int r = R2 * n1 + n2;
+            a[n1] = (r == 0) ? x[0] : cmul(x[r], w(r));
+        }
+        Dft<R1, T>::run(a);
+        static_for<0, R1>([&](auto k1c) {
+            constexpr int k1 = decltype(k1c)::value;
+            y[n2 * R1 + k1] = twiddle_const<R, n2 * k1>(a[k1]);
+        });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+        cpx<T> b[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) b[n2] = y[n2 * R1 + k1];
+        Dft<R2, T>::run(b);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = b[k2];
+    }
+}
+
+template <int R, typename T>
+struct DftTw {
+    template <typename TW>
+    static __device__ __forceinline__ void run(cpx<T>* x, const TW& w) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w(r));
+        Dft<R, T>::run(x);
+    }
+};
+template <typename T>
+struct DftTw<16, T> {
+    template <typename TW>
+    static __device__ __forceinline__ void run(cpx<T>* x, const TW& w) { dft_split_tw<4, 4, T>(x, w); }
+};
+template <typename T>
+struct DftTw<24, T> {
+    template <typename TW>
+    static __device__ __forceinline__ void run(cpx<T>* x, const TW& w) { dft_split_tw<8, 3, T>(x, w); }
+};
+
 // DFTs whose upper half of inputs is zero (x[R/2 .. R-1] == 0), used by the
 // first stage of a zero-padded transform.
 template <int R, typename T>
@@ -370,10 +422,28 @@ using SmemRow = SmemCol<T, 0>;
 template <typename T, int C>
 struct SmemColSkew {
     cpx<T>* base;
+    int unused;  // same initialiser shape as SmemCol
     __device__ __forceinline__ cpx<T>& operator[](int i) const { return base[C * (i + (i >> 4))]; }
 };
 // Complex slots of a skewed exchange buffer of C columns of n elements.
 __host__ __device__ constexpr int skew_slots(int n, int C) { return C * (n + (n >> 4)); }
+
+// Exchange view for C interleaved columns of a static kernel: once the C
+// columns of one element index fill a 128-byte wavefront (C·sizeof(cpx<T>) ≥
+// 128), a stride of C + 1 already spreads a warp's accesses evenly and needs
+// no index arithmetic; narrower groups take the skewed layout.
+template <typename T>
+__host__ __device__ constexpr bool xchg_skewed(int C) { return C * (int)sizeof(cpx<T>) < 128; }
+template <typename T, int C>
+using XchgCol = typename std::conditional<xchg_skewed<T>(C), SmemColSkew<T, C>, SmemCol<T, C + 1>>::type;
+template <typename T>
+__host__ __device__ constexpr int xchg_slots(int n, int C) { return xchg_skewed<T>(C) ? skew_slots(n, C) : n * (C + 1); }
+// A TMA-loaded [n][C] tile that later serves as the exchange: plain stride C
+// for full wavefronts, else skewed (the tile then occupies the first n·C slots).
+template <typename T, int C>
+using TileCol = typename std::conditional<xchg_skewed<T>(C), SmemColSkew<T, C>, SmemCol<T, C>>::type;
+template <typename T>
+__host__ __device__ constexpr int tile_slots(int n, int C) { return xchg_skewed<T>(C) ? skew_slots(n, C) : n * C; }
 // Complex slots of one row-layout buffer of n elements.
 __host__ __device__ constexpr int padded_row(int n) { return n + (n >> 4) + 1; }
 
@@ -524,21 +594,16 @@ __device__ __forceinline__ void stage_static(cpx<T> (&v)[NCOL][E], int t, const 
         const int j = t + TF * u;
         const int jm = j % Ns;
         const int base = (j - jm) * R + jm;
-        cpx<T> w[R];
-        if constexpr (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) w[r] = tw[jm * r * TWS];
-        }
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) {
             cpx<T> x[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r] = v[c][u + r * B];
             if constexpr (Ns > 1) {
-#pragma unroll
-                for (int r = 1; r < R; ++r) x[r] = cmul(x[r], w[r]);
+                DftTw<R, T>::run(x, [&](int r) { return tw[jm * r * TWS]; });
+            } else {
+                Dft<R, T>::run(x);
             }
-            Dft<R, T>::run(x);
             if constexpr (LAST) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) v[c][u + r * B] = x[r];

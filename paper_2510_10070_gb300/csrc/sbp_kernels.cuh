@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass
     }
     __syncthreads();  // twiddles visible
     if constexpr (CS > 0) {
-        const SmemCol<T, xstride(CS)> buf[1] = {{xb + c, 0}};
+        const XchgCol<T, CS> buf[1] = {{xb + c, 0}};
         fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
     } else {
         const SmemCol<T> buf[1] = {{xb + c, xstride(C)}};
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass
 // [NS][CS] column tile of plane z into shared memory with cp.async.bulk.tensor
 // on an mbarrier, the tile then serves as the FFT's exchange buffer, and the
 // results are stored straight from registers.
-// smem: tile [NS][CS] (128-byte aligned) | tw[NS] | mbarrier
+// smem: tile [NS][CS] (128-byte aligned; later the exchange, TileCol) | tw[NS] | mbarrier
 template <typename T, int E, bool INV, int NS, int CS>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
     k_y_tma(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A, TmaCtl ctl,
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
     constexpr int BOXR = NS < 256 ? NS : 256;  // rows per TMA box (box dimensions are at most 256)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     cpx<T>* tile = reinterpret_cast<cpx<T>*>(smem_raw);
-    cpx<T>* tw = tile + NS * C;
+    cpx<T>* tw = tile + tile_slots<T>(NS, C);  // the tile, then the FFT's exchange
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NS);
     const int tid = threadIdx.x;
     const int a0 = blockIdx.x * C;
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
         const cpx<T> x = tile[(t + Tf * e) * C + c];
         v[0][e] = INV ? cconj(x) : x;
     }
-    const SmemCol<T, C> buf[1] = {{tile + c, 0}};
+    const TileCol<T, C> buf[1] = {{tile + c, 0}};
     fft_static<NS, E, 0, 1, T>(v, t, tw, buf);  // first exchange write follows a barrier
     if (a < A.h) {
         cpx<T>* dst = W + ((size_t)row0 + t) * A.pitch + a;
@@ -671,7 +671,7 @@ __device__ __forceinline__ T green_factor(const GreenCoef<T>& q, int m, int ms, 
 // elements t + Tf·e of the padded column; the zero half (e ≥ E/2) never enters
 // the pruned first stage, and of the inverse only the kept half (outputs < N)
 // is stored, so the compiler drops the rest of the last stage.
-// smem: twM[M] | green[C] | exchange [M][xstride(C)]
+// smem: twM[M] | green[C] | exchange of C columns of M (XchgCol)
 template <typename T, int E, int N>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
                                                           const cpx<T>* __restrict__ twMg, const T* __restrict__ /*unused*/,
@@ -679,7 +679,6 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padde
     constexpr int M = 2 * N;
     constexpr int Tf = M / E;
     constexpr int C = zpad_cols(N, E, sizeof(T) == 8);
-    constexpr int XS = xstride(C);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* twM = reinterpret_cast<cpx<T>*>(smem_raw);
     GreenT<T>* gm = reinterpret_cast<GreenT<T>*>(twM + M);
@@ -714,7 +713,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padde
             v[0][e] = x;
         }
     }
-    const SmemCol<T, XS> buf[1] = {{xb + c, 0}};
+    const XchgCol<T, C> buf[1] = {{xb + c, 0}};
     fft_static_padded<M, E, 1, T>(v, t, twM, buf);  // starts with a barrier: tables are visible
 
     {
@@ -760,7 +759,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padde
 //   k = 0: table value (L²/2 at k_z = 0)
 // The second form adds no cancellation of its own in FP32: 1 - e^{-kL} comes
 // from expm1 and 1 - cos(k_z L) from the FP64 host tables.
-// smem: twM[M] | table [2N+1][4] | green[C] | skewed exchange of C columns
+// smem: twM[M] | table [2N+1][4] | green[C] | exchange of C columns (XchgCol)
 template <typename T, int E, int N>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_paper(
     cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/, const cpx<T>* __restrict__ twMg,
@@ -809,7 +808,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_paper
             v[0][e] = x;
         }
     }
-    const SmemColSkew<T, C> buf[1] = {{xb + c}};
+    const XchgCol<T, C> buf[1] = {{xb + c, 0}};
     fft_static_quarter<M, E, 1, T>(v, t, twM, buf);  // starts with a barrier: tables are visible
 
     {

@@ -125,7 +125,9 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     const auto xsm = [&](int C) { return (size_t)nx * cs + (size_t)C * padded_row(nx) * cs; };
     while (Cx > 1 && ((ny / 2) % Cx != 0 || xsm(Cx) > kSmemLimit)) --Cx;
     int Cy = std::min(std::max(1, std::min(16, kMaxThreads / py.Tf)), h);
-    const auto ysm = [&](int C) { return (size_t)ny * cs + (size_t)ny * xstride(C) * cs; };
+    const auto ysm = [&](int C) {
+        return (size_t)ny * cs + std::max((size_t)ny * xstride(C), (size_t)xchg_slots<float>(ny, C)) * cs;
+    };
     if (is_static_len<float>(ny)) {
         Cy = ypass_cols(ny, false);  // compiled into the static y kernel
     } else {
