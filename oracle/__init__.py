@@ -32,4 +32,7 @@ from .vgf import (  # noqa: F401
     solve_at,
     plane_sums,
     k0_potential,
+    remap_phase,
+    remap_y,
+    solve_physical,
 )

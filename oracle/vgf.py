@@ -64,6 +64,9 @@ __all__ = [
     "solve_at",
     "plane_sums",
     "k0_potential",
+    "remap_phase",
+    "remap_y",
+    "solve_physical",
 ]
 
 
@@ -326,3 +329,61 @@ def k0_potential(S, nx: int, ny: int, nz: int, p: SolveParams):
     for i in range(nz):
         out[i] = sum(c[i - j + nz - 1] * S[j] for j in range(nz))
     return 4.0 * np.pi * p.G * out / (nx * ny)
+
+
+# ---------------------------------------------------------------------------
+# Mapping to the periodic frame (Sect. 2.1: "Mapping to fully periodic
+# points", spectral variant, i.e. shear advection by Fourier interpolation).
+#
+# The k(t) of Sect. 2.1 (k_x = K_x + (Δy0/L_x) K_y) is the wave-vector of a
+# field f that obeys f(x + L_x, y) = f(x, y + Δy0) seen through the frame
+# f̃(x, y) = f(x, y - s x), s = Δy0/L_x: f̃ is periodic in x, and a periodic-
+# frame mode exp(i(K_x x + K_y y)) is the physical mode with k_x = K_x + s K_y.
+# Step 1 of the scheme maps ρ → ρ̃, step 2 solves for Φ̃ (``solve``), step 3
+# maps Φ̃ back: Φ(x, y) = Φ̃(x, y + s x).  Each x-column is shifted in y by a
+# Fourier interpolation; x is the cell centre -L_x/2 + (i + ½) dx (any other
+# origin only translates ρ̃ and Φ̃ in y, which cancels between steps 1 and 3).
+# The Nyquist coefficient (K_y = -π N_y/L_y) is multiplied by the real part of
+# its phase factor (the same reading as Ĝ_eff on the Nyquist planes): the
+# shifted column stays real.
+# ---------------------------------------------------------------------------
+
+def remap_phase(nx: int, Lx: float, Ly: float, dy0: float):
+    """u_i = s x_i / L_y = (Δy0/L_y)(x_i/L_x) for every cell centre x_i (shape [nx])."""
+    xi = (np.arange(nx) + 0.5) / nx - 0.5
+    return (dy0 / Ly) * xi
+
+
+def remap_y(f, u, sign: float):
+    """Shift every x-column of f [..., ny, nx] by sign·u_x·L_y in y.
+
+    sign = -1 maps the physical frame to the periodic one (ρ̃(x, y) = ρ(x, y - s x)),
+    sign = +1 maps back.  Naive DFT along y, coefficient K_y(b) multiplied by
+    exp(sign·2πi b_s u_x) (b_s signed, |b_s| < ny/2) and by cos(π ny u_x) on the
+    Nyquist row, then the naive inverse DFT; the result is real.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    ny, nx = f.shape[-2], f.shape[-1]
+    u = np.asarray(u, dtype=np.float64)
+    F = np.einsum("by,...yx->...bx", _dft_matrix(ny, -1.0), f)
+    bs = signed_index(np.arange(ny), ny).astype(np.float64)
+    ph = np.exp(sign * 2j * np.pi * np.outer(bs, u))  # [ny, nx]
+    if ny % 2 == 0:
+        ph[ny // 2, :] = np.cos(np.pi * ny * u)
+    F = F * ph
+    g = np.einsum("yb,...bx->...yx", _dft_matrix(ny, +1.0), F) / ny
+    return g.real.copy()
+
+
+def solve_physical(rho, p: SolveParams, t: float):
+    """Φ in the physical (shearing) frame for a physical-frame density ρ [nz, ny, nx].
+
+    The three steps of Sect. 2.1 in order: map ρ to the periodic frame, solve
+    there (``solve``), map Φ̃ back.
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    u = remap_phase(nx, p.Lx, p.Ly, shear_offset(p.q, p.Omega, p.Lx, p.Ly, t))
+    rho_t = remap_y(rho, u, -1.0)
+    phi_t = solve(rho_t, p, t)
+    return remap_y(phi_t, u, +1.0)
