@@ -166,8 +166,27 @@ enum {
      * padding is built for power-of-two nz from 32 to 512 (FP32) or 256
      * (FP64); other nz return SBP_ERR_UNSUPPORTED_SIZE and keep the old
      * setting.  SBP_OPT_Z_VARIANT then accepts only 0. */
-    SBP_OPT_TRUNCATION = 6
+    SBP_OPT_TRUNCATION = 6,
+    /* Frame of rho and phi (Sect. 2.1, "Mapping to fully periodic points").
+     * 0 (default): the periodic frame, rho~(x, y) = rho(x, y - s x) with
+     * s = Delta y0 / Lx, and phi~ returned in the same frame.  1: the
+     * physical (shearing) frame: the plan maps rho to the periodic frame by
+     * Fourier interpolation of every x-column in y (phase exp(-i K_y s x);
+     * the Nyquist row takes the real part of its phase), solves, and maps
+     * phi back (phase exp(+i K_y s x)).  The mapping is fused into y
+     * transforms that run before the x transforms, so a solve still makes
+     * five passes.  x is the cell centre -Lx/2 + (i + 1/2) dx.  Built for nx
+     * and ny in {32, 64, 96, 128, 192, 256, 512, 1024}; other sizes return
+     * SBP_ERR_UNSUPPORTED_SIZE and keep the old setting.  sbp_run_stage
+     * returns SBP_ERR_INVALID_ARG while it is 1. */
+    SBP_OPT_FRAME = 7
 };
+
+/* sbp_last_cuda_error — the CUDA runtime's message for the error behind the
+ * calling thread's most recent SBP_ERR_CUDA from a kernel launch (a static
+ * string; "no CUDA error recorded" if there was none).  Not part of the
+ * paper's method: a diagnostic of this library. */
+const char* sbp_last_cuda_error(void);
 
 /* sbp_plan_set_option — set a plan option (see the enum above).  Unknown
  * options or values return SBP_ERR_INVALID_ARG.  Not to be called while a

@@ -95,6 +95,16 @@ struct sbp_plan_s {
     // the vertical transform to pad = 4 times nz (else 2)
     double alpha = 1.0;
     int pad = 2;
+    // z-pass geometry: stored columns per row, rows per plane, row pitch
+    int zh = 0, zrows = 0, zpitch = 0;
+    // physical frame (SBP_OPT_FRAME = 1): y-first passes with the mapping of Sect. 2.1
+    int frame = 0;
+    void* ry_fwd = nullptr;
+    void* ry_inv = nullptr;
+    void* rows_fwd = nullptr;
+    void* rows_inv = nullptr;
+    int ry_threads = 0, ry_tiles = 0, ry_green_blocks = 0, rows_threads = 0, rows_grid = 0;
+    size_t ry_smem = 0, rows_smem = 0;
     void* z_fn = nullptr;      // the z-pass kernel of the chosen variant
     int green_blocks = 0;      // x-forward blocks that fill the Green's table
     // fused xy plane kernels (square planes with a built kernel), used by solves
@@ -131,6 +141,16 @@ struct sbp_plan_s {
 namespace {
 
 bool f64_of(const sbp_plan_s* p) { return p->dtype == SBP_F64; }
+
+// The CUDA error behind the calling thread's last SBP_ERR_CUDA from a launch.
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+sbp_status launch_status() {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return SBP_OK;
+    g_last_cuda = e;
+    return SBP_ERR_CUDA;
+}
 
 template <typename T>
 size_t zpass_smem(int n, int C) {
@@ -257,7 +277,7 @@ bool configure_z(sbp_plan_s* p, int variant) {
         p->zp.C = C;
         p->zp.threads = C * P.Tf;
         p->zp.smem = smem;
-        p->zp.grid = dim3((unsigned)((p->h + C - 1) / C), (unsigned)p->ny, 1);
+        p->zp.grid = dim3((unsigned)((p->zh + C - 1) / C), (unsigned)p->zrows, 1);
         p->z_variant = 0;
         p->z_padded = false;
         p->z_fn = reinterpret_cast<void*>(fn);
@@ -286,7 +306,7 @@ bool configure_z(sbp_plan_s* p, int variant) {
     if (padded) {
         C = zpad_cols(p->nz, E, f64);  // compiled into the kernel
     } else {
-        C = std::min(C, p->h);
+        C = std::min(C, p->zh);
         while (C > 1 && smem(C) > kSmemBudget) --C;
     }
     if (C * per_col > kMaxThreads || smem(C) > kSmemBudget) return false;
@@ -299,7 +319,7 @@ bool configure_z(sbp_plan_s* p, int variant) {
     p->zp.C = C;
     p->zp.threads = C * per_col;
     p->zp.smem = smem(C);
-    p->zp.grid = dim3((unsigned)((p->h + C - 1) / C), (unsigned)p->ny, 1);
+    p->zp.grid = dim3((unsigned)((p->zh + C - 1) / C), (unsigned)p->zrows, 1);
     p->z_variant = variant;
     p->z_padded = padded;
     p->z_fn = reinterpret_cast<void*>(fn);
@@ -488,10 +508,11 @@ sbp_status upload_tables(sbp_plan_s* p) {
     const size_t o_twM4 = take(4 * (size_t)p->nz * cs);
     const size_t o_ptab = take(ptab.size() * sizeof(T));
     const size_t o_c00 = take((2 * (size_t)p->nz) * sizeof(double));
-    const size_t o_ts = take((size_t)tiles * sizeof(double));
+    const int ry_tiles = (p->nx / 2 + ypass_cols(p->ny, !f32) - 1) / ypass_cols(p->ny, !f32) * p->nz;
+    const size_t o_ts = take((size_t)std::max(tiles, ry_tiles) * sizeof(double));
     const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
     const size_t o_err = take(sizeof(int));
-    const size_t o_green = take((size_t)p->h * p->ny * sizeof(GreenT<T>));
+    const size_t o_green = take(std::max((size_t)p->h * p->ny, (size_t)p->nx * (p->ny / 2 + 1)) * sizeof(GreenT<T>));
     p->tables_bytes = off;
     if (cudaMalloc(&p->tables, off) != cudaSuccess) {
         cudaGetLastError();
@@ -592,10 +613,11 @@ struct DeviceGuard {
 GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
     GreenFill g;
     g.tab = p->green;
-    const int total = p->h * p->ny;
+    const int total = p->frame ? p->nx * (p->ny / 2 + 1) : p->h * p->ny;
     g.per_block = (total + blocks - 1) / blocks;
     g.nx = p->nx;
     g.ny = p->ny;
+    g.yhalf = p->frame;
     g.Lx = p->Lx;
     g.Ly = p->Ly;
     g.L = p->alpha * p->Lz;
@@ -638,9 +660,9 @@ template <typename T>
 ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     ZArgs a;
     a.P = p->pz;
-    a.pitch = p->pitch;
-    a.h = p->h;
-    a.ny = p->ny;
+    a.pitch = p->zpitch;
+    a.h = p->zh;
+    a.ny = p->zrows;
     a.C = p->zp.C;
     a.L = p->alpha * p->Lz;
     a.kzc = (M_PI / p->Lz) * (M_PI / p->Lz);
@@ -650,7 +672,7 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     a.zero_k0 = f32 ? 1 : 0;
     a.green = p->green;
     a.tile_sums = p->tile_sums;
-    a.tiles_per_plane = p->xy_fused ? p->xy_cluster : (p->ny / 2) / p->xf.C;
+    a.tiles_per_plane = p->frame ? p->ry_tiles : (p->xy_fused ? p->xy_cluster : (p->ny / 2) / p->xf.C);
     a.c00 = p->c00;
     a.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
     a.vk0 = (f32 && with_k0) ? p->vk0 : nullptr;
@@ -741,7 +763,7 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
         default:
             return SBP_ERR_INVALID_ARG;
     }
-    return cudaGetLastError() == cudaSuccess ? SBP_OK : SBP_ERR_CUDA;
+    return launch_status();
 }
 
 // Launch a fused xy plane kernel: one cluster of xy_cluster CTAs per z-plane.
@@ -795,9 +817,112 @@ sbp_status solve_fused_t(sbp_plan_s* p, const void* rho, void* phi, double t, cu
                      static_cast<const cpx<T>*>(p->W), static_cast<T*>(phi), tw, b);
 }
 
+// Physical-frame solve (SBP_OPT_FRAME = 1): y pass with the forward mapping
+// and the Green's table, forward x rows, z pass, inverse x rows, y pass with
+// the mapping back.
+template <typename T>
+sbp_status solve_physical_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
+                            const double* s_dev) {
+    const bool f32 = !f64_of(p);
+    RArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nx = p->nx;
+    a.ny = p->ny;
+    a.pitch = p->nx;
+    a.pairs = p->nx / 2;
+    a.tiles = p->ry_tiles;
+    a.green_blocks = p->ry_green_blocks;
+    a.gf = make_green_fill(p, t, p->ry_green_blocks);
+    a.gf.s_dev = s_dev;
+    a.s = shear_s(p, t);
+    a.s_dev = s_dev;
+    a.lx_over_ly = p->Lx / p->Ly;
+    a.vk0 = f32 ? p->vk0 : nullptr;
+    cpx<T>* W = static_cast<cpx<T>*>(p->W);
+    const int rows = p->nz * (p->ny / 2 + 1);
+    using RY = RemapKernels<T>;
+    reinterpret_cast<decltype(RY::ry_fwd)>(p->ry_fwd)<<<p->ry_green_blocks + p->ry_tiles * p->nz, p->ry_threads,
+                                                         p->ry_smem, st>>>(
+        static_cast<const T*>(rho), W, static_cast<const cpx<T>*>(p->tw_y), f32 ? p->tile_sums : nullptr, a);
+    reinterpret_cast<decltype(RY::rows_fwd)>(p->rows_fwd)<<<p->rows_grid, p->rows_threads, p->rows_smem, st>>>(
+        W, static_cast<const cpx<T>*>(p->tw_x), rows, p->nx);
+    reinterpret_cast<ZKernel<T>>(p->z_fn)<<<p->zp.grid, p->zp.threads, p->zp.smem, st>>>(
+        W, static_cast<const cpx<T>*>(p->tw_z),
+        static_cast<const cpx<T>*>(p->pad == 4 ? p->tw_M4 : (p->z_padded ? p->tw_M : p->tw_2z)),
+        static_cast<const T*>(p->kz2), make_zargs<T>(p, true));
+    reinterpret_cast<decltype(RY::rows_inv)>(p->rows_inv)<<<p->rows_grid, p->rows_threads, p->rows_smem, st>>>(
+        W, static_cast<const cpx<T>*>(p->tw_x), rows, p->nx);
+    reinterpret_cast<decltype(RY::ry_inv)>(p->ry_inv)<<<p->ry_tiles * p->nz, p->ry_threads, p->ry_smem, st>>>(
+        W, static_cast<T*>(phi), static_cast<const cpx<T>*>(p->tw_y), a);
+    return launch_status();
+}
+
+// Frame of rho and phi (SBP_OPT_FRAME): 0 = periodic frame (the default
+// passes), 1 = physical frame.  Returns false, leaving the plan unchanged,
+// when the physical-frame kernels are not built for (nx, ny) or do not fit.
+template <typename T>
+bool configure_frame(sbp_plan_s* p, int frame) {
+    const int old_zh = p->zh, old_zrows = p->zrows, old_zpitch = p->zpitch, old_frame = p->frame;
+    auto restore = [&]() {
+        p->frame = old_frame;
+        p->zh = old_zh;
+        p->zrows = old_zrows;
+        p->zpitch = old_zpitch;
+        configure_z<T>(p, p->z_variant);
+    };
+    if (frame == 0) {
+        p->frame = 0;
+        p->zh = p->h;
+        p->zrows = p->ny;
+        p->zpitch = p->pitch;
+        if (!configure_z<T>(p, p->z_variant) && !configure_z<T>(p, 0)) {
+            restore();
+            return false;
+        }
+        return true;
+    }
+    const RemapKernels<T> k = remap_kernels_for<T>(p->nx, p->ny);
+    if (!k.ry_fwd || !k.ry_inv || !k.rows_fwd || !k.rows_inv) return false;
+    const size_t cs = sizeof(cpx<T>);
+    const int tfy = p->ny / k.ry_E, tfx = p->nx / k.rows_E;
+    const int rows_C = kMaxThreads / tfx;
+    const size_t ry_smem = (size_t)p->ny * cs + (size_t)xchg_slots<T>(p->ny, k.ry_C) * cs;
+    const size_t rows_smem = (size_t)p->nx * cs + (size_t)rows_C * padded_row(p->nx) * cs;
+    if (rows_C < 1 || k.ry_C * tfy > kMaxThreads || ry_smem > kSmemBudget || rows_smem > kSmemBudget) return false;
+    const void* fns[4] = {reinterpret_cast<const void*>(k.ry_fwd), reinterpret_cast<const void*>(k.ry_inv),
+                          reinterpret_cast<const void*>(k.rows_fwd), reinterpret_cast<const void*>(k.rows_inv)};
+    for (const void* f : fns) {
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    p->frame = 1;
+    p->zh = p->nx;
+    p->zrows = p->ny / 2 + 1;
+    p->zpitch = p->nx;
+    if (!configure_z<T>(p, p->z_variant) && !configure_z<T>(p, 0)) {
+        restore();
+        return false;
+    }
+    p->ry_fwd = reinterpret_cast<void*>(k.ry_fwd);
+    p->ry_inv = reinterpret_cast<void*>(k.ry_inv);
+    p->rows_fwd = reinterpret_cast<void*>(k.rows_fwd);
+    p->rows_inv = reinterpret_cast<void*>(k.rows_inv);
+    p->ry_threads = k.ry_C * tfy;
+    p->ry_tiles = (p->nx / 2 + k.ry_C - 1) / k.ry_C;
+    p->ry_green_blocks = (p->nx * (p->ny / 2 + 1) + p->ry_threads - 1) / p->ry_threads;
+    p->ry_smem = ry_smem;
+    p->rows_threads = rows_C * tfx;
+    p->rows_grid = (p->nz * (p->ny / 2 + 1) + rows_C - 1) / rows_C;
+    p->rows_smem = rows_smem;
+    return true;
+}
+
 template <typename T>
 sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
                    const double* s_dev = nullptr) {
+    if (p->frame) return solve_physical_t<T>(p, rho, phi, t, st, s_dev);
     if (p->xy_fused) return solve_fused_t<T>(p, rho, phi, t, st, s_dev);
     sbp_status s;
     if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true, s_dev)) != SBP_OK) return s;
@@ -1041,6 +1166,9 @@ sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz, double Lx, dou
     p->rsize = f64 ? sizeof(double) : sizeof(float);
     p->h = nx / 2 + 1;
     p->pitch = (p->h + 1) / 2 * 2;
+    p->zh = p->h;
+    p->zrows = ny;
+    p->zpitch = p->pitch;
     if (!build_fft_plan(nx, plan_E(nx, f64), p->px) || !build_fft_plan(ny, plan_E(ny, f64), p->py)) {
         delete p;
         return SBP_ERR_UNSUPPORTED_SIZE;
@@ -1051,7 +1179,8 @@ sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz, double Lx, dou
         delete p;
         return SBP_ERR_UNSUPPORTED_SIZE;
     }
-    p->W_bytes = (size_t)nz * ny * p->pitch * 2 * p->rsize;
+    // the physical-frame passes store the y half spectrum, [nz][ny/2+1][nx]
+    p->W_bytes = std::max((size_t)nz * ny * p->pitch, (size_t)nz * (ny / 2 + 1) * nx) * 2 * p->rsize;
     if (cudaMalloc(&p->W, p->W_bytes) != cudaSuccess) {
         cudaGetLastError();
         p->W = nullptr;
@@ -1158,6 +1287,10 @@ void sbp_plan_destroy(sbp_plan p) {
     }
 }
 
+const char* sbp_last_cuda_error(void) {
+    return g_last_cuda == cudaSuccess ? "no CUDA error recorded" : cudaGetErrorString(g_last_cuda);
+}
+
 const char* sbp_status_string(sbp_status s) {
     switch (s) {
         case SBP_OK: return "ok";
@@ -1176,13 +1309,20 @@ const char* sbp_status_string(sbp_status s) {
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
     if (option == SBP_OPT_Y_TMA || option == SBP_OPT_XY_PASSES || option == SBP_OPT_Z_VARIANT ||
-        option == SBP_OPT_TRUNCATION) {
+        option == SBP_OPT_TRUNCATION || option == SBP_OPT_FRAME) {
         // captured batch graphs hold the old kernels and arguments
         DeviceGuard g(p->device);
         if (!g.ok) return SBP_ERR_CUDA;
         cudaDeviceSynchronize();
         cudaGetLastError();
         drop_executors(p);
+    }
+    if (option == SBP_OPT_FRAME) {
+        if (value != 0.0 && value != 1.0) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        const bool ok = f64_of(p) ? configure_frame<double>(p, (int)value) : configure_frame<float>(p, (int)value);
+        return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
     }
     if (option == SBP_OPT_TRUNCATION) {
         if (!(value == 1.0 || (value > 1.0 && value <= 3.0))) return SBP_ERR_INVALID_ARG;
@@ -1264,6 +1404,7 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int*
 
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream) {
     if (!p || !out || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (p->frame != 0) return SBP_ERR_INVALID_ARG;  // the stages are the periodic-frame passes
     if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_FILL) return SBP_ERR_INVALID_ARG;
     if (stage != SBP_STAGE_GREEN_TABLE && stage != SBP_STAGE_GREEN_FILL && !in) return SBP_ERR_INVALID_ARG;
     if ((stage == SBP_STAGE_Y_FORWARD || stage == SBP_STAGE_Z_CONVOLVE || stage == SBP_STAGE_Y_INVERSE) &&

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "sbp_kernels.cuh"
+#include "sbp_remap.cuh"
 #include "sbp_xy.cuh"
 
 namespace sbp {
@@ -162,6 +163,70 @@ inline XYKernels<T> xy_kernels_for(int n, int variant) {
     SBP_XY_LIST(SBP_MATCH_XY)
 #undef SBP_MATCH_XY
     return XYKernels<T>{};
+}
+
+// Physical-frame passes (static lengths): y kernels with the mapping of
+// Sect. 2.1 fused in (length ny) and complex row transforms (length nx).
+template <typename T>
+struct RemapKernels {
+    void (*ry_fwd)(const T*, cpx<T>*, const cpx<T>*, double*, RArgs) = nullptr;
+    void (*ry_inv)(const cpx<T>*, T*, const cpx<T>*, RArgs) = nullptr;
+    int ry_E = 0, ry_C = 0;
+    void (*rows_fwd)(cpx<T>*, const cpx<T>*, int, int) = nullptr;
+    void (*rows_inv)(cpx<T>*, const cpx<T>*, int, int) = nullptr;
+    int rows_E = 0;
+};
+#define SBP_DECLARE_REMAP(T, TAG, N) \
+    RemapKernels<T> remap_y_##TAG##_n##N(); \
+    RemapKernels<T> remap_x_##TAG##_n##N();
+SBP_N_LIST_F32(SBP_DECLARE_REMAP)
+SBP_N_LIST_F64(SBP_DECLARE_REMAP)
+#define SBP_DEFINE_REMAP_Y(T, TAG, N)                                  \
+    RemapKernels<T> remap_y_##TAG##_n##N() {                           \
+        constexpr int E = plan_E(N, sizeof(T) == 8);                   \
+        constexpr int CP = ypass_cols(N, sizeof(T) == 8);              \
+        RemapKernels<T> k;                                             \
+        k.ry_fwd = k_ry_forward<T, E, N, CP>;                          \
+        k.ry_inv = k_ry_inverse<T, E, N, CP>;                          \
+        k.ry_E = E;                                                    \
+        k.ry_C = CP;                                                   \
+        return k;                                                      \
+    }
+#define SBP_DEFINE_REMAP_X(T, TAG, N)                                  \
+    RemapKernels<T> remap_x_##TAG##_n##N() {                           \
+        constexpr int E = plan_E(N, sizeof(T) == 8);                   \
+        RemapKernels<T> k;                                             \
+        k.rows_fwd = k_rows_c2c<T, E, N, false>;                       \
+        k.rows_inv = k_rows_c2c<T, E, N, true>;                        \
+        k.rows_E = E;                                                  \
+        return k;                                                      \
+    }
+
+// The y kernels for ny merged with the row kernels for nx (null if not built).
+template <typename T>
+inline RemapKernels<T> remap_kernels_for(int nx, int ny) {
+    RemapKernels<T> r, x;
+#define SBP_MATCH_REMAP(TT, TAG, N)                                                     \
+    if (std::is_same<T, TT>::value && ny == N) {                                        \
+        auto k = remap_y_##TAG##_n##N();                                                \
+        r.ry_fwd = reinterpret_cast<decltype(r.ry_fwd)>(k.ry_fwd);                      \
+        r.ry_inv = reinterpret_cast<decltype(r.ry_inv)>(k.ry_inv);                      \
+        r.ry_E = k.ry_E;                                                                \
+        r.ry_C = k.ry_C;                                                                \
+    }                                                                                   \
+    if (std::is_same<T, TT>::value && nx == N) {                                        \
+        auto k = remap_x_##TAG##_n##N();                                                \
+        x.rows_fwd = reinterpret_cast<decltype(x.rows_fwd)>(k.rows_fwd);                \
+        x.rows_inv = reinterpret_cast<decltype(x.rows_inv)>(k.rows_inv);                \
+        x.rows_E = k.rows_E;                                                            \
+    }
+    SBP_N_LIST_F32(SBP_MATCH_REMAP)
+    SBP_N_LIST_F64(SBP_MATCH_REMAP)
+#undef SBP_MATCH_REMAP
+    r.rows_fwd = x.rows_fwd;
+    r.rows_inv = x.rows_inv;
+    r.rows_E = x.rows_E;
+    return r;
 }
 
 // True when length n has static kernels for type T.

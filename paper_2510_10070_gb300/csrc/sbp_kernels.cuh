@@ -45,9 +45,10 @@ struct GreenT {
 // Work a pass kernel may do on the side: fill the Green's table for modes
 // [blockIdx.x·per_block, …) (FP64 arithmetic, rounded to the table type).
 struct GreenFill {
-    void* tab;  // GreenT<T>[ny][nx/2+1] or null
+    void* tab;  // GreenT<T>[ny][nx/2+1] (yhalf: [ny/2+1][nx]) or null
     int per_block;
     int nx, ny;
+    int yhalf;  // stored modes: 0 = half in x (periodic-frame passes), 1 = half in y
     double Lx, Ly, L, s;
     const double* s_dev;  // if set, s is read from device memory (batched executor)
 };
@@ -164,7 +165,29 @@ __device__ __forceinline__ FF ff_add_f(FF a, float b) {
     return {h, l};
 }
 
-// Green's-function parameters of stored mode (a, b), a ∈ [0, nx/2], b ∈ [0, ny):
+// Block-wide double-float sum of every thread's partial; the result is valid
+// in thread 0.  Contains a barrier.  The last warp may be partial, so only
+// lanes that exist are added.
+__device__ __forceinline__ FF block_sum_ff(FF acc) {
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int wl = min(32, (int)blockDim.x - warp * 32);
+    const unsigned mask = (wl == 32) ? 0xffffffffu : ((1u << wl) - 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF other = {__shfl_xor_sync(mask, acc.hi, o), __shfl_xor_sync(mask, acc.lo, o)};
+        if ((lane ^ o) < wl) acc = ff_add(acc, other);
+    }
+    __shared__ FF wsum[kMaxThreads / 32];
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    FF tot = {0.f, 0.f};
+    if (tid == 0)
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot = ff_add(tot, wsum[w]);
+    return tot;
+}
+
+// Green's-function parameters of stored mode (a, b), unsigned FFT indices a < nx, b < ny:
 // |k|² and 1 - e^{-|k| L} for the mode and for its Hermitian partner
 // (Sect. 2.1 wave-vector k_x = K_x + s K_y; Eq. Green's function regularized
 // in Fourier needs e^{-kL}).  FP64 throughout.
@@ -211,8 +234,8 @@ template <typename T>
 __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     if (gf.tab == nullptr) return;
     GreenT<T>* tab = static_cast<GreenT<T>*>(gf.tab);
-    const int h = gf.nx / 2 + 1;
-    const int total = h * gf.ny;
+    const int h = gf.yhalf ? gf.nx : gf.nx / 2 + 1;  // stored modes per row
+    const int total = h * (gf.yhalf ? gf.ny / 2 + 1 : gf.ny);
     const int q0 = block * gf.per_block;
     const int q1 = min(total, q0 + gf.per_block);
     const double s = gf.s_dev != nullptr ? *gf.s_dev : gf.s;
@@ -315,26 +338,10 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forw
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 kahan_add(acc, (float)v[0][e].x);
-            kahan_add(acc, (float)v[0][e].y);
+                kahan_add(acc, (float)v[0][e].y);
             }
-            // block reduction; the last warp may be partial, so only lanes
-            // that exist are added
-            const int lane = tid & 31, warp = tid >> 5;
-            const int wl = min(32, (int)blockDim.x - warp * 32);
-            const unsigned mask = (wl == 32) ? 0xffffffffu : ((1u << wl) - 1u);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                FF other = {__shfl_xor_sync(mask, acc.hi, o), __shfl_xor_sync(mask, acc.lo, o)};
-                if ((lane ^ o) < wl) acc = ff_add(acc, other);
-            }
-            __shared__ FF wsum[kMaxThreads / 32];
-            if (lane == 0) wsum[warp] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                FF tot = {0.f, 0.f};
-                for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot = ff_add(tot, wsum[w]);
-                tile_sums[bid] = (double)tot.hi + (double)tot.lo;
-            }
+            const FF tot = block_sum_ff(acc);
+            if (tid == 0) tile_sums[bid] = (double)tot.hi + (double)tot.lo;
         }
     }
     __syncthreads();  // twiddles visible

@@ -230,6 +230,7 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     xa.gf.per_block = (h * ny + gblocks - 1) / gblocks;
     xa.gf.nx = nx;
     xa.gf.ny = ny;
+    xa.gf.yhalf = 0;
     xa.gf.Lx = Lx;
     xa.gf.Ly = Ly;
     xa.gf.L = Lz;

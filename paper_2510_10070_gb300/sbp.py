@@ -51,12 +51,15 @@ class Option(IntEnum):
     SPIN_BUDGET = 4
     DEBUG_WITHHOLD_COPY = 5
     TRUNCATION = 6
+    FRAME = 7
 
 
 class SbpError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = Status(status) if status in Status._value2member_map_ else status
         msg = lib().sbp_status_string(int(status)).decode() if _lib is not None else str(status)
+        if _lib is not None and int(status) == int(Status.CUDA):
+            msg += " (" + lib().sbp_last_cuda_error().decode() + ")"
         super().__init__(f"{where}: {msg} (status {int(status)})")
 
 
@@ -73,6 +76,7 @@ SIGNATURES = {
                                    ctypes.POINTER(_c_double), _vp]),
     "sbp_plan_destroy": (None, [_vp]),
     "sbp_status_string": (ctypes.c_char_p, [_c_int]),
+    "sbp_last_cuda_error": (ctypes.c_char_p, []),
     "sbp_plan_set_option": (_c_int, [_vp, _c_int, _c_double]),
     "sbp_plan_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_size_t)]),
