@@ -35,4 +35,6 @@ from .vgf import (  # noqa: F401
     remap_phase,
     remap_y,
     solve_physical,
+    fill_ghosts,
+    force,
 )

@@ -67,6 +67,8 @@ __all__ = [
     "remap_phase",
     "remap_y",
     "solve_physical",
+    "fill_ghosts",
+    "force",
 ]
 
 
@@ -387,3 +389,48 @@ def solve_physical(rho, p: SolveParams, t: float):
     rho_t = remap_y(rho, u, -1.0)
     phi_t = solve(rho_t, p, t)
     return remap_y(phi_t, u, +1.0)
+
+
+# ---------------------------------------------------------------------------
+# Ghost cells and forces (Sect. 2.4, last paragraph): beyond the last active
+# cell in z the potential keeps that cell's gradient, i.e. the ghost layers
+# continue Φ linearly.  The force g = -∇Φ uses second-order central
+# differences; in z the ghost rule makes them one-sided in the boundary cells.
+# Horizontally Φ is periodic in y and, in x, periodic in the periodic frame or
+# shear-periodic in the physical frame: Φ(x + L_x, y) = Φ(x, y + Δy0), the
+# shifted neighbour column taken by the same Fourier interpolation as the
+# mapping of Sect. 2.1.
+# ---------------------------------------------------------------------------
+
+def fill_ghosts(phi, ng: int):
+    """[nz + 2 ng, ny, nx]: phi in the middle, ng linearly continued layers on each side."""
+    phi = np.asarray(phi, dtype=np.float64)
+    nz = phi.shape[0]
+    out = np.empty((nz + 2 * ng,) + phi.shape[1:], dtype=np.float64)
+    out[ng:ng + nz] = phi
+    top = phi[nz - 1] - phi[nz - 2]  # gradient of the last active cell (per dz)
+    bot = phi[1] - phi[0]
+    for g in range(1, ng + 1):
+        out[ng + nz - 1 + g] = phi[nz - 1] + g * top
+        out[ng - g] = phi[0] - g * bot
+    return out
+
+
+def force(phi, p: SolveParams, t: float, physical: bool):
+    """g = -∇Φ, shape [3, nz, ny, nx] (x, y, z components), at the cell centres."""
+    phi = np.asarray(phi, dtype=np.float64)
+    nz, ny, nx = phi.shape
+    dx, dy, dz = p.Lx / nx, p.Ly / ny, p.Lz / nz
+    right = np.roll(phi, -1, axis=2)  # Φ(x + dx)
+    left = np.roll(phi, 1, axis=2)  # Φ(x - dx)
+    if physical:
+        dy0 = shear_offset(p.q, p.Omega, p.Lx, p.Ly, t)
+        # neighbour of the last column: Φ(x_0 + L_x, y) = Φ(x_0, y + Δy0)
+        right[:, :, nx - 1] = remap_y(phi[:, :, 0:1], np.array([dy0 / p.Ly]), +1.0)[:, :, 0]
+        # neighbour of the first column: Φ(x_{nx-1} - L_x, y) = Φ(x_{nx-1}, y - Δy0)
+        left[:, :, 0] = remap_y(phi[:, :, nx - 1:nx], np.array([dy0 / p.Ly]), -1.0)[:, :, 0]
+    gx = -(right - left) / (2.0 * dx)
+    gy = -(np.roll(phi, -1, axis=1) - np.roll(phi, 1, axis=1)) / (2.0 * dy)
+    ext = fill_ghosts(phi, 1)
+    gz = -(ext[2:] - ext[:-2]) / (2.0 * dz)
+    return np.stack([gx, gy, gz])
