@@ -182,6 +182,30 @@ enum {
     SBP_OPT_FRAME = 7
 };
 
+/* sbp_fill_ghosts — vertical ghost layers of a solution (Sect. 2.4, last
+ * paragraph: the ghost cells keep the gradient of the last active cell).
+ * phi: device pointer, [nz][ny][nx] of the plan's real type (a result of
+ * sbp_solve).  out: device pointer, [nz + 2 ng][ny][nx]; planes ng .. ng+nz-1
+ * receive phi, and for g = 1 .. ng
+ *   out[ng + nz - 1 + g] = phi[nz-1] + g (phi[nz-1] - phi[nz-2]),
+ *   out[ng - g]          = phi[0]    - g (phi[1]    - phi[0]).
+ * ng in [1, 16].  Both pointers 16-byte aligned and not overlapping, else
+ * SBP_ERR_INVALID_ARG.  Asynchronous on `stream`.  Horizontal ghosts are the
+ * caller's (periodic, or shear-periodic in the physical frame). */
+sbp_status sbp_fill_ghosts(sbp_plan p, const void* phi, void* out, int ng, void* stream);
+
+/* sbp_force — g = -grad(phi) at the cell centres by second-order central
+ * differences, the force that the ghost rule of Sect. 2.4 serves.
+ * phi: device pointer, [nz][ny][nx]; force: device pointer, [3][nz][ny][nx]
+ * (x, y, z components).  y is periodic.  x is periodic when the plan's frame
+ * (SBP_OPT_FRAME) is the periodic one; in the physical frame it is
+ * shear-periodic at time t, phi(x + Lx, y) = phi(x, y + Delta y0(t)), the two
+ * boundary neighbours taken by Fourier interpolation in y.  In z the ghost
+ * rule makes the differences one-sided in the first and last planes.
+ * Pointers 16-byte aligned and not overlapping, t finite, else
+ * SBP_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+sbp_status sbp_force(sbp_plan p, const void* phi, void* force, double t, void* stream);
+
 /* sbp_last_cuda_error — the CUDA runtime's message for the error behind the
  * calling thread's most recent SBP_ERR_CUDA from a kernel launch (a static
  * string; "no CUDA error recorded" if there was none).  Not part of the

@@ -103,6 +103,7 @@ struct sbp_plan_s {
     void* ry_inv = nullptr;
     void* rows_fwd = nullptr;
     void* rows_inv = nullptr;
+    void* shear_cols = nullptr;
     int ry_threads = 0, ry_tiles = 0, ry_green_blocks = 0, rows_threads = 0, rows_grid = 0;
     size_t ry_smem = 0, rows_smem = 0;
     void* z_fn = nullptr;      // the z-pass kernel of the chosen variant
@@ -128,6 +129,7 @@ struct sbp_plan_s {
     double* c00 = nullptr;
     double* tile_sums = nullptr;
     double* vk0 = nullptr;    // FP64 mean-mode potential per plane (FP32 path)
+    void* side = nullptr;     // [nz][2][ny] shifted boundary columns (physical-frame force)
     void* green = nullptr;    // GreenT<T>[ny][nx/2+1] for the current solve
     int* err = nullptr;       // device status word: 1 after a bounded wait gave up
     // TMA y passes (static ny): tile loads of the half spectrum
@@ -512,6 +514,7 @@ sbp_status upload_tables(sbp_plan_s* p) {
     const size_t o_ts = take((size_t)std::max(tiles, ry_tiles) * sizeof(double));
     const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
     const size_t o_err = take(sizeof(int));
+    const size_t o_side = take((size_t)p->nz * 2 * p->ny * sizeof(T));
     const size_t o_green = take(std::max((size_t)p->h * p->ny, (size_t)p->nx * (p->ny / 2 + 1)) * sizeof(GreenT<T>));
     p->tables_bytes = off;
     if (cudaMalloc(&p->tables, off) != cudaSuccess) {
@@ -528,6 +531,7 @@ sbp_status upload_tables(sbp_plan_s* p) {
     p->tile_sums = reinterpret_cast<double*>(base + o_ts);
     p->vk0 = reinterpret_cast<double*>(base + o_vk0);
     p->err = reinterpret_cast<int*>(base + o_err);
+    p->side = base + o_side;
     p->tw_M = base + o_twM;
     p->tw_M4 = base + o_twM4;
     p->paper_tab = base + o_ptab;
@@ -882,15 +886,16 @@ bool configure_frame(sbp_plan_s* p, int frame) {
         return true;
     }
     const RemapKernels<T> k = remap_kernels_for<T>(p->nx, p->ny);
-    if (!k.ry_fwd || !k.ry_inv || !k.rows_fwd || !k.rows_inv) return false;
+    if (!k.ry_fwd || !k.ry_inv || !k.rows_fwd || !k.rows_inv || !k.shear_cols) return false;
     const size_t cs = sizeof(cpx<T>);
     const int tfy = p->ny / k.ry_E, tfx = p->nx / k.rows_E;
     const int rows_C = kMaxThreads / tfx;
     const size_t ry_smem = (size_t)p->ny * cs + (size_t)xchg_slots<T>(p->ny, k.ry_C) * cs;
     const size_t rows_smem = (size_t)p->nx * cs + (size_t)rows_C * padded_row(p->nx) * cs;
     if (rows_C < 1 || k.ry_C * tfy > kMaxThreads || ry_smem > kSmemBudget || rows_smem > kSmemBudget) return false;
-    const void* fns[4] = {reinterpret_cast<const void*>(k.ry_fwd), reinterpret_cast<const void*>(k.ry_inv),
-                          reinterpret_cast<const void*>(k.rows_fwd), reinterpret_cast<const void*>(k.rows_inv)};
+    const void* fns[5] = {reinterpret_cast<const void*>(k.ry_fwd), reinterpret_cast<const void*>(k.ry_inv),
+                          reinterpret_cast<const void*>(k.rows_fwd), reinterpret_cast<const void*>(k.rows_inv),
+                          reinterpret_cast<const void*>(k.shear_cols)};
     for (const void* f : fns) {
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
             cudaGetLastError();
@@ -909,6 +914,7 @@ bool configure_frame(sbp_plan_s* p, int frame) {
     p->ry_inv = reinterpret_cast<void*>(k.ry_inv);
     p->rows_fwd = reinterpret_cast<void*>(k.rows_fwd);
     p->rows_inv = reinterpret_cast<void*>(k.rows_inv);
+    p->shear_cols = reinterpret_cast<void*>(k.shear_cols);
     p->ry_threads = k.ry_C * tfy;
     p->ry_tiles = (p->nx / 2 + k.ry_C - 1) / k.ry_C;
     p->ry_green_blocks = (p->nx * (p->ny / 2 + 1) + p->ry_threads - 1) / p->ry_threads;
@@ -1127,6 +1133,28 @@ sbp_status set_truncation(sbp_plan_s* p, double alpha) {
     return st;
 }
 
+template <typename T>
+sbp_status force_t(sbp_plan_s* p, const T* phi, T* force, double t, cudaStream_t st) {
+    const T* side = nullptr;
+    if (p->frame == 1) {
+        using RY = RemapKernels<T>;
+        const double u = shear_s(p, t) * p->Lx / p->Ly;  // Δy0 / L_y
+        const int tf = p->ny / plan_E(p->ny, f64_of(p));
+        const int cp = shear_cols_planes(tf);
+        const size_t smem = (size_t)p->ny * sizeof(cpx<T>) + (size_t)xchg_slots<T>(p->ny, cp) * sizeof(cpx<T>);
+        reinterpret_cast<decltype(RY::shear_cols)>(p->shear_cols)<<<(p->nz + cp - 1) / cp, cp * tf, smem, st>>>(
+            phi, static_cast<T*>(p->side), static_cast<const cpx<T>*>(p->tw_y), p->nx, p->nz, u);
+        side = static_cast<const T*>(p->side);
+    }
+    constexpr int ZC = 16;
+    const dim3 block(32, 8);
+    const dim3 grid((unsigned)((p->nx + 31) / 32), (unsigned)((p->ny + 7) / 8), (unsigned)((p->nz + ZC - 1) / ZC));
+    const double dx = p->Lx / p->nx, dy = p->Ly / p->ny, dz = p->Lz / p->nz;
+    k_force<T, ZC><<<grid, block, 0, st>>>(phi, force, side, p->nx, p->ny, p->nz, (T)(0.5 / dx), (T)(0.5 / dy),
+                                           (T)(1.0 / dz));
+    return launch_status();
+}
+
 }  // namespace
 
 extern "C" {
@@ -1285,6 +1313,39 @@ void sbp_plan_destroy(sbp_plan p) {
         drop_executors(p);
         free_plan(p);
     }
+}
+
+sbp_status sbp_fill_ghosts(sbp_plan p, const void* phi, void* out, int ng, void* stream) {
+    if (!p || !phi || !out || ng < 1 || ng > 16) return SBP_ERR_INVALID_ARG;
+    if (!aligned16(phi) || !aligned16(out)) return SBP_ERR_INVALID_ARG;
+    const size_t plane = (size_t)p->nx * p->ny;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(phi), b0 = reinterpret_cast<uintptr_t>(out);
+    const size_t abytes = plane * p->nz * p->rsize, bbytes = plane * (p->nz + 2 * ng) * p->rsize;
+    if (a0 < b0 + bbytes && b0 < a0 + abytes) return SBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const dim3 grid((unsigned)((plane + 255) / 256), (unsigned)(p->nz + 2 * ng));
+    if (f64_of(p))
+        k_fill_ghosts<double><<<grid, 256, 0, st>>>(static_cast<const double*>(phi), static_cast<double*>(out),
+                                                    (int)plane, p->nz, ng);
+    else
+        k_fill_ghosts<float><<<grid, 256, 0, st>>>(static_cast<const float*>(phi), static_cast<float*>(out),
+                                                   (int)plane, p->nz, ng);
+    return launch_status();
+}
+
+sbp_status sbp_force(sbp_plan p, const void* phi, void* force, double t, void* stream) {
+    if (!p || !phi || !force || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (!aligned16(phi) || !aligned16(force)) return SBP_ERR_INVALID_ARG;
+    const size_t n = (size_t)p->nx * p->ny * p->nz * p->rsize;
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(phi), b0 = reinterpret_cast<uintptr_t>(force);
+    if (a0 < b0 + 3 * n && b0 < a0 + n) return SBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return SBP_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return f64_of(p) ? force_t<double>(p, static_cast<const double*>(phi), static_cast<double*>(force), t, st)
+                     : force_t<float>(p, static_cast<const float*>(phi), static_cast<float*>(force), t, st);
 }
 
 const char* sbp_last_cuda_error(void) {

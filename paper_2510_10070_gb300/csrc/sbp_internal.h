@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "sbp_kernels.cuh"
+#include "sbp_force.cuh"
 #include "sbp_remap.cuh"
 #include "sbp_xy.cuh"
 
@@ -175,6 +176,8 @@ struct RemapKernels {
     void (*rows_fwd)(cpx<T>*, const cpx<T>*, int, int) = nullptr;
     void (*rows_inv)(cpx<T>*, const cpx<T>*, int, int) = nullptr;
     int rows_E = 0;
+    // shifted boundary columns for the physical-frame force (length ny)
+    void (*shear_cols)(const T*, T*, const cpx<T>*, int, int, double) = nullptr;
 };
 #define SBP_DECLARE_REMAP(T, TAG, N) \
     RemapKernels<T> remap_y_##TAG##_n##N(); \
@@ -188,6 +191,7 @@ SBP_N_LIST_F64(SBP_DECLARE_REMAP)
         RemapKernels<T> k;                                             \
         k.ry_fwd = k_ry_forward<T, E, N, CP>;                          \
         k.ry_inv = k_ry_inverse<T, E, N, CP>;                          \
+        k.shear_cols = k_shear_cols<T, E, N, shear_cols_planes(N / E)>; \
         k.ry_E = E;                                                    \
         k.ry_C = CP;                                                   \
         return k;                                                      \
@@ -211,6 +215,7 @@ inline RemapKernels<T> remap_kernels_for(int nx, int ny) {
         auto k = remap_y_##TAG##_n##N();                                                \
         r.ry_fwd = reinterpret_cast<decltype(r.ry_fwd)>(k.ry_fwd);                      \
         r.ry_inv = reinterpret_cast<decltype(r.ry_inv)>(k.ry_inv);                      \
+        r.shear_cols = reinterpret_cast<decltype(r.shear_cols)>(k.shear_cols);          \
         r.ry_E = k.ry_E;                                                                \
         r.ry_C = k.ry_C;                                                                \
     }                                                                                   \

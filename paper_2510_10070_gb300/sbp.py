@@ -77,6 +77,8 @@ SIGNATURES = {
     "sbp_plan_destroy": (None, [_vp]),
     "sbp_status_string": (ctypes.c_char_p, [_c_int]),
     "sbp_last_cuda_error": (ctypes.c_char_p, []),
+    "sbp_fill_ghosts": (_c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_int, ctypes.c_void_p]),
+    "sbp_force": (_c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _c_double, ctypes.c_void_p]),
     "sbp_plan_set_option": (_c_int, [_vp, _c_int, _c_double]),
     "sbp_plan_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(ctypes.c_size_t)]),
@@ -178,6 +180,28 @@ class Plan:
         import torch
 
         return torch.zeros((self.nz, self.ny, self.spectrum_pitch, 2), dtype=self.torch_dtype, device="cuda")
+
+    def fill_ghosts(self, phi, ng: int, out=None, stream=None):
+        """phi with ng vertical ghost layers on each side (gradient of the last active cell kept)."""
+        import torch
+
+        self._check_tensor(phi, "phi")
+        if out is None:
+            out = torch.empty((self.nz + 2 * ng, self.ny, self.nx), dtype=self.torch_dtype, device=phi.device)
+        _check(lib().sbp_fill_ghosts(self._h, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     int(ng), _stream_handle(stream)), "sbp_fill_ghosts")
+        return out
+
+    def force(self, phi, t: float = 0.0, out=None, stream=None):
+        """g = -∇Φ, shape [3, nz, ny, nx], in the plan's frame at shear time t."""
+        import torch
+
+        self._check_tensor(phi, "phi")
+        if out is None:
+            out = torch.empty((3, self.nz, self.ny, self.nx), dtype=self.torch_dtype, device=phi.device)
+        _check(lib().sbp_force(self._h, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                               float(t), _stream_handle(stream)), "sbp_force")
+        return out
 
     def run_stage(self, stage, inp, out, t: float = 0.0, stream=None):
         ip = ctypes.c_void_p(inp.data_ptr()) if inp is not None else None
