@@ -37,4 +37,7 @@ from .vgf import (  # noqa: F401
     solve_physical,
     fill_ghosts,
     force,
+    green_periodic,
+    sasha_mean_terms,
+    solve_sasha,
 )

@@ -69,6 +69,9 @@ __all__ = [
     "solve_physical",
     "fill_ghosts",
     "force",
+    "green_periodic",
+    "sasha_mean_terms",
+    "solve_sasha",
 ]
 
 
@@ -434,3 +437,68 @@ def force(phi, p: SolveParams, t: float, physical: bool):
     ext = fill_ghosts(phi, 1)
     gz = -(ext[2:] - ext[:-2]) / (2.0 * dz)
     return np.stack([gx, gy, gz])
+
+
+# ---------------------------------------------------------------------------
+# SASHA (Sect. 2.2): Φ = Φ0 + Φ_P.  Φ0(z) = 4πG ρ̄ z (z/2 - z0) solves
+# ∇²Φ0 = 4πG ρ̄ (ρ̄ the volume mean, z0 = <z ρ>/<ρ> the centre of mass);
+# Φ_P solves ∇²Φ_P = 4πG (ρ - ρ̄) spectrally, Eq. (Poisson spectral)
+# Φ̂ = -4πG ρ̂/|k|² (0 at k = 0), with the density zero-padded in z to 2 nz
+# (Sect. 2.4, zero-padding paragraph) and k = (k_x(t), k_y, k_z) of the padded
+# grid.  Readings: the volume averages are cell sums over the box; z is the
+# cell centre measured from the box centre (another origin changes Φ by a
+# constant); z0 = 0 when the total mass is zero; on the sheared Nyquist planes
+# the kernel is averaged with the Hermitian partner, as for VGF.
+#
+# The printed Φ0 and the reported accuracy disagree for off-centre mass: the
+# periodic solve on 2 L_z gives Φ_P the edge slope 4πG ρ̄ z0 / 2 (half of what
+# the vacuum condition Φ'(L_z/2) = -Φ'(-L_z/2) needs with the printed Φ0), so
+# Φ keeps a uniform field: a residual -2πG ρ̄ z0 z.  ``centre`` selects the
+# vertex of Φ0: 1 is the printed form (vertex at z0), 1/2 puts it at z0/2,
+# which cancels the residual and gives the third-order 1D convergence that
+# Sect. 3.3 reports for the shifted Gaussian.
+# ---------------------------------------------------------------------------
+
+def green_periodic(k, kz, k_is_zero):
+    """-1/(k² + k_z²) of Eq. (Poisson spectral), 0 at k = 0, k_z = 0."""
+    k = np.asarray(k, dtype=np.float64)
+    kz = np.asarray(kz, dtype=np.float64)
+    k, kz, zero_k = np.broadcast_arrays(k, kz, np.asarray(k_is_zero, dtype=bool))
+    den = k * k + kz * kz
+    out = np.zeros(k.shape, dtype=np.float64)
+    nz_ = ~(zero_k & (kz == 0.0))
+    out[nz_] = -1.0 / den[nz_]
+    return out
+
+
+def sasha_mean_terms(rho, Lz: float):
+    """(ρ̄, z0) of Sect. 2.2 from cell sums; z = cell centres from the box centre."""
+    rho = np.asarray(rho, dtype=np.float64)
+    nz = rho.shape[0]
+    S = plane_sums(rho)
+    z = (np.arange(nz) + 0.5) * (Lz / nz) - 0.5 * Lz
+    total = math.fsum(S)
+    rbar = total / rho.size
+    z0 = math.fsum(z * S) / total if total != 0.0 else 0.0
+    return rbar, z0
+
+
+def solve_sasha(rho, p: SolveParams, t: float, centre: float = 1.0):
+    """Φ̃ by SASHA for a periodic-frame density ρ̃ [nz, ny, nx] (pad = 2 nz).
+
+    Φ0 = 4πG ρ̄ z (z/2 - centre·z0).
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    nz, ny, nx = rho.shape
+    rbar, z0 = sasha_mean_terms(rho, p.Lz)
+    R = horizontal_dft(rho - rbar)
+    s = shear_offset(p.q, p.Omega, p.Lx, p.Ly, t) / p.Lx
+    k1, k2, is_zero = mode_wavenumbers(nx, ny, p.Lx, p.Ly, s)
+    _, kz = _kz_signed(nz, p.Lz, 2)
+    g1 = green_periodic(k1[..., None], kz[None, None, :], is_zero[..., None])
+    g2 = green_periodic(k2[..., None], kz[None, None, :], is_zero[..., None])
+    c = vertical_kernel(0.5 * (g1 + g2), nz, 2)
+    phi_p = 4.0 * np.pi * p.G * inverse_horizontal_dft(vertical_convolve(c, R))
+    z = (np.arange(nz) + 0.5) * (p.Lz / nz) - 0.5 * p.Lz
+    phi0 = 4.0 * np.pi * p.G * rbar * z * (0.5 * z - centre * z0)
+    return phi_p + phi0[:, None, None]
