@@ -179,7 +179,19 @@ enum {
      * and ny in {32, 64, 96, 128, 192, 256, 512, 1024}; other sizes return
      * SBP_ERR_UNSUPPORTED_SIZE and keep the old setting.  sbp_run_stage
      * returns SBP_ERR_INVALID_ARG while it is 1. */
-    SBP_OPT_FRAME = 7
+    SBP_OPT_FRAME = 7,
+    /* Method (Sect. 2.2 and 2.3).  0 (default): VGF-HybridBC, the truncated
+     * Green's function of Eq. (Green's function regularized in Fourier).
+     * 1 and 2: SASHA, Phi = Phi0 + Phi_P with Phi0(z) = 4 pi G rho_mean z
+     * (z/2 - zeta) for the volume-mean density and Phi_P from Eq. (Poisson
+     * spectral), -4 pi G rho^/|k|^2, for rho - rho_mean zero-padded to 2 nz.
+     * 1: zeta = z0 = <z rho>/<rho> as printed; 2: zeta = z0/2, the vertex that
+     * cancels the uniform field -2 pi G rho_mean z0 which the 2 Lz period
+     * otherwise leaves for off-centre mass.  z is the cell centre measured
+     * from the box centre.  Requires SBP_OPT_TRUNCATION = 1 (else
+     * SBP_ERR_UNSUPPORTED_SIZE, either order); sbp_run_stage returns
+     * SBP_ERR_INVALID_ARG while it is not 0. */
+    SBP_OPT_METHOD = 8
 };
 
 /* sbp_fill_ghosts — vertical ghost layers of a solution (Sect. 2.4, last

@@ -95,6 +95,9 @@ struct sbp_plan_s {
     // the vertical transform to pad = 4 times nz (else 2)
     double alpha = 1.0;
     int pad = 2;
+    // method (SBP_OPT_METHOD): 0 = VGF-HybridBC, 1 = SASHA with Φ0's vertex at z0
+    // (as printed), 2 = SASHA with the vertex at z0/2
+    int method = 0;
     // z-pass geometry: stored columns per row, rows per plane, row pitch
     int zh = 0, zrows = 0, zpitch = 0;
     // physical frame (SBP_OPT_FRAME = 1): y-first passes with the mapping of Sect. 2.1
@@ -344,6 +347,7 @@ bool configure_xy(sbp_plan_s* p, int variant) {
         return true;
     }
     if (p->nx != p->ny || (variant != 2 && variant != 3)) return false;
+    if (f64_of(p) && p->method != 0) return false;  // the FP64 plane kernels make no plane sums
     const XYKernels<T> k = xy_kernels_for<T>(p->nx, variant - 1);
     if (!k.fwd || !k.inv || k.smem_fwd > kSmemBudget || k.smem_inv > kSmemBudget) return false;
     if (cudaFuncSetAttribute(k.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess ||
@@ -454,6 +458,24 @@ void host_c00(std::vector<double>& c, int nz, double Lz, int pad, double L) {
             long long ph = ((long long)m * n) % M;
             if (ph < 0) ph += M;
             acc += g[m + M / 2] * std::cos(kTwoPi * (double)ph / (double)M);
+        }
+        c[n + nz - 1] = acc / (double)M;
+    }
+}
+
+// SASHA: the k = 0 column of Eq. (Poisson spectral) on the 2 nz padded grid,
+// c_n = (1/M) Σ_{m ≠ 0} (-1/k_z²) cos(2π m n / M), k_z = π m / Lz.
+void host_c00_periodic(std::vector<double>& c, int nz, double Lz) {
+    const int M = 2 * nz;
+    c.assign(2 * (size_t)nz - 1, 0.0);
+    for (int n = -(nz - 1); n <= nz - 1; ++n) {
+        double acc = 0.0;
+        for (int m = -nz; m < nz; ++m) {
+            if (m == 0) continue;
+            const double kz = M_PI * (double)m / Lz;
+            long long ph = ((long long)m * n) % M;
+            if (ph < 0) ph += M;
+            acc += (-1.0 / (kz * kz)) * std::cos(kTwoPi * (double)ph / (double)M);
         }
         c[n + nz - 1] = acc / (double)M;
     }
@@ -572,9 +594,12 @@ sbp_status refresh_vertical_tables(sbp_plan_s* p) {
         cudaGetLastError();
         return SBP_ERR_CUDA;
     }
-    if (!f64_of(p)) {
+    if (!f64_of(p) || p->method != 0) {
         std::vector<double> c00;
-        host_c00(c00, p->nz, p->Lz, p->pad, p->alpha * p->Lz);
+        if (p->method != 0)
+            host_c00_periodic(c00, p->nz, p->Lz);
+        else
+            host_c00(c00, p->nz, p->Lz, p->pad, p->alpha * p->Lz);
         if (cudaMemcpy(p->c00, c00.data(), c00.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             return SBP_ERR_CUDA;
@@ -614,6 +639,33 @@ struct DeviceGuard {
     }
 };
 
+// SASHA k = 0 column (see SashaArgs).  smem: S[nz] doubles (dynamic)
+__global__ void __launch_bounds__(256) k_sasha_k0(SashaArgs A) {
+    extern __shared__ double S[];
+    __shared__ double red[2 * (256 / 32)];
+    const int tid = threadIdx.x;
+    const int nz = A.nz;
+    const double dz = A.Lz / nz;
+    double s1 = 0.0, s2 = 0.0;
+    for (int j = tid; j < nz; j += blockDim.x) {
+        double sacc = 0.0;
+        for (int q = 0; q < A.tiles_per_plane; ++q) sacc += A.tile_sums[(size_t)j * A.tiles_per_plane + q];
+        S[j] = sacc;
+        s1 += sacc;
+        s2 += (-0.5 * A.Lz + (j + 0.5) * dz) * sacc;
+    }
+    const double2 tot = block_sum_d2(make_double2(s1, s2), red);  // its barriers also publish S
+    const double rbar = tot.x / (A.cells_xy * nz);
+    const double zeta = A.centre * (tot.x != 0.0 ? tot.y / tot.x : 0.0);
+    const double sub = rbar * A.cells_xy;
+    for (int i = tid; i < nz; i += blockDim.x) {
+        double acc = 0.0;
+        for (int j = 0; j < nz; ++j) acc += A.c00[i - j + nz - 1] * (S[j] - sub);
+        const double zi = -0.5 * A.Lz + (i + 0.5) * dz;
+        A.vk0[i] = A.k0_coef * acc + A.fourpiG * rbar * zi * (0.5 * zi - zeta);
+    }
+}
+
 GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
     GreenFill g;
     g.tab = p->green;
@@ -624,10 +676,27 @@ GreenFill make_green_fill(const sbp_plan_s* p, double t, int blocks) {
     g.yhalf = p->frame;
     g.Lx = p->Lx;
     g.Ly = p->Ly;
-    g.L = p->alpha * p->Lz;
+    g.L = p->method != 0 ? HUGE_VAL : p->alpha * p->Lz;  // SASHA: e^{-kL} = 0, Ĝ = -1/|k|²
     g.s = shear_s(p, t);
     g.s_dev = nullptr;
     return g;
+}
+
+// SASHA: the k = 0 column after the z pass (the x or y inverse pass adds it).
+sbp_status launch_sasha_k0(const sbp_plan_s* p, int tiles_per_plane, cudaStream_t st) {
+    SashaArgs a;
+    a.tile_sums = p->tile_sums;
+    a.tiles_per_plane = tiles_per_plane;
+    a.nz = p->nz;
+    a.c00 = p->c00;
+    a.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
+    a.fourpiG = 4.0 * M_PI * p->G;
+    a.cells_xy = (double)p->nx * p->ny;
+    a.Lz = p->Lz;
+    a.centre = p->method == 2 ? 0.5 : 1.0;
+    a.vk0 = p->vk0;
+    k_sasha_k0<<<1, 256, (size_t)p->nz * sizeof(double), st>>>(a);
+    return launch_status();
 }
 
 template <typename T>
@@ -673,13 +742,15 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
     a.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * (double)p->pad * p->nz);
     a.paper_tab = p->paper_tab;
     const bool f32 = !f64_of(p);
-    a.zero_k0 = f32 ? 1 : 0;
+    const bool side_k0 = f32 || p->method != 0;  // k = 0 column on the FP64 side path
+    a.zero_k0 = side_k0 ? 1 : 0;
     a.green = p->green;
     a.tile_sums = p->tile_sums;
     a.tiles_per_plane = p->frame ? p->ry_tiles : (p->xy_fused ? p->xy_cluster : (p->ny / 2) / p->xf.C);
     a.c00 = p->c00;
     a.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
-    a.vk0 = (f32 && with_k0) ? p->vk0 : nullptr;
+    // SASHA's k = 0 column comes from k_sasha_k0 after the z pass
+    a.vk0 = (side_k0 && with_k0 && p->method == 0) ? p->vk0 : nullptr;
     return a;
 }
 
@@ -703,7 +774,7 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
                 a.gf.s_dev = s_dev;
                 grid.x += p->green_blocks;
             }
-            double* sums = (f32 && fused) ? p->tile_sums : nullptr;
+            double* sums = ((f32 || p->method != 0) && fused) ? p->tile_sums : nullptr;
             kx.x_fwd<<<grid, p->xf.threads, p->xf.smem, st>>>(static_cast<const T*>(in), W,
                                                              static_cast<const cpx<T>*>(p->tw_x), sums, a);
             break;
@@ -734,6 +805,10 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
                 W, static_cast<const cpx<T>*>(p->tw_z),
                 static_cast<const cpx<T>*>(p->pad == 4 ? p->tw_M4 : (p->z_padded ? p->tw_M : p->tw_2z)),
                 static_cast<const T*>(p->kz2), make_zargs<T>(p, fused));
+            if (fused && p->method != 0) {
+                const sbp_status s = launch_sasha_k0(p, make_zargs<T>(p, true).tiles_per_plane, st);
+                if (s != SBP_OK) return s;
+            }
             break;
         case SBP_STAGE_Y_INVERSE:
             if (p->y_tma) {
@@ -753,7 +828,7 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
             break;
         case SBP_STAGE_X_INVERSE: {
             XArgs a = make_xargs<T>(p);
-            if (f32 && fused) a.vk0 = p->vk0;
+            if ((f32 || p->method != 0) && fused) a.vk0 = p->vk0;
             kx.x_inv<<<p->xi.grid, p->xi.threads, p->xi.smem, st>>>(
                 static_cast<const cpx<T>*>(in), static_cast<T*>(out), static_cast<const cpx<T>*>(p->tw_x), a);
             break;
@@ -841,19 +916,24 @@ sbp_status solve_physical_t(sbp_plan_s* p, const void* rho, void* phi, double t,
     a.s = shear_s(p, t);
     a.s_dev = s_dev;
     a.lx_over_ly = p->Lx / p->Ly;
-    a.vk0 = f32 ? p->vk0 : nullptr;
+    a.vk0 = (f32 || p->method != 0) ? p->vk0 : nullptr;
     cpx<T>* W = static_cast<cpx<T>*>(p->W);
     const int rows = p->nz * (p->ny / 2 + 1);
     using RY = RemapKernels<T>;
     reinterpret_cast<decltype(RY::ry_fwd)>(p->ry_fwd)<<<p->ry_green_blocks + p->ry_tiles * p->nz, p->ry_threads,
                                                          p->ry_smem, st>>>(
-        static_cast<const T*>(rho), W, static_cast<const cpx<T>*>(p->tw_y), f32 ? p->tile_sums : nullptr, a);
+        static_cast<const T*>(rho), W, static_cast<const cpx<T>*>(p->tw_y),
+        (f32 || p->method != 0) ? p->tile_sums : nullptr, a);
     reinterpret_cast<decltype(RY::rows_fwd)>(p->rows_fwd)<<<p->rows_grid, p->rows_threads, p->rows_smem, st>>>(
         W, static_cast<const cpx<T>*>(p->tw_x), rows, p->nx);
     reinterpret_cast<ZKernel<T>>(p->z_fn)<<<p->zp.grid, p->zp.threads, p->zp.smem, st>>>(
         W, static_cast<const cpx<T>*>(p->tw_z),
         static_cast<const cpx<T>*>(p->pad == 4 ? p->tw_M4 : (p->z_padded ? p->tw_M : p->tw_2z)),
         static_cast<const T*>(p->kz2), make_zargs<T>(p, true));
+    if (p->method != 0) {
+        const sbp_status s = launch_sasha_k0(p, p->ry_tiles, st);
+        if (s != SBP_OK) return s;
+    }
     reinterpret_cast<decltype(RY::rows_inv)>(p->rows_inv)<<<p->rows_grid, p->rows_threads, p->rows_smem, st>>>(
         W, static_cast<const cpx<T>*>(p->tw_x), rows, p->nx);
     reinterpret_cast<decltype(RY::ry_inv)>(p->ry_inv)<<<p->ry_tiles * p->nz, p->ry_threads, p->ry_smem, st>>>(
@@ -1117,6 +1197,21 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
 }
 
 template <typename T>
+sbp_status set_method(sbp_plan_s* p, int method) {
+    const int old = p->method;
+    p->method = method;
+    sbp_status st = refresh_vertical_tables<T>(p);
+    // FP64 SASHA needs plane sums, which only the separate x passes make
+    if (st == SBP_OK && f64_of(p) && method != 0 && p->xy_fused && !configure_xy<T>(p, 1))
+        st = SBP_ERR_UNSUPPORTED_SIZE;
+    if (st != SBP_OK) {
+        p->method = old;
+        refresh_vertical_tables<T>(p);
+    }
+    return st;
+}
+
+template <typename T>
 sbp_status set_truncation(sbp_plan_s* p, double alpha) {
     const double old_alpha = p->alpha;
     const int old_pad = p->pad;
@@ -1370,7 +1465,7 @@ const char* sbp_status_string(sbp_status s) {
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
     if (option == SBP_OPT_Y_TMA || option == SBP_OPT_XY_PASSES || option == SBP_OPT_Z_VARIANT ||
-        option == SBP_OPT_TRUNCATION || option == SBP_OPT_FRAME) {
+        option == SBP_OPT_TRUNCATION || option == SBP_OPT_FRAME || option == SBP_OPT_METHOD) {
         // captured batch graphs hold the old kernels and arguments
         DeviceGuard g(p->device);
         if (!g.ok) return SBP_ERR_CUDA;
@@ -1385,8 +1480,17 @@ sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
         const bool ok = f64_of(p) ? configure_frame<double>(p, (int)value) : configure_frame<float>(p, (int)value);
         return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
     }
+    if (option == SBP_OPT_METHOD) {
+        const int v = (int)value;
+        if ((double)v != value || v < 0 || v > 2) return SBP_ERR_INVALID_ARG;
+        if (v != 0 && p->pad != 2) return SBP_ERR_UNSUPPORTED_SIZE;  // SASHA pads to 2 nz
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        return f64_of(p) ? set_method<double>(p, v) : set_method<float>(p, v);
+    }
     if (option == SBP_OPT_TRUNCATION) {
         if (!(value == 1.0 || (value > 1.0 && value <= 3.0))) return SBP_ERR_INVALID_ARG;
+        if (value != 1.0 && p->method != 0) return SBP_ERR_UNSUPPORTED_SIZE;  // SASHA pads to 2 nz
         DeviceGuard g(p->device);
         if (!g.ok) return SBP_ERR_CUDA;
         return f64_of(p) ? set_truncation<double>(p, value) : set_truncation<float>(p, value);
@@ -1465,7 +1569,7 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int*
 
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream) {
     if (!p || !out || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
-    if (p->frame != 0) return SBP_ERR_INVALID_ARG;  // the stages are the periodic-frame passes
+    if (p->frame != 0 || p->method != 0) return SBP_ERR_INVALID_ARG;  // the stages are the VGF periodic-frame passes
     if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_FILL) return SBP_ERR_INVALID_ARG;
     if (stage != SBP_STAGE_GREEN_TABLE && stage != SBP_STAGE_GREEN_FILL && !in) return SBP_ERR_INVALID_ARG;
     if ((stage == SBP_STAGE_Y_FORWARD || stage == SBP_STAGE_Z_CONVOLVE || stage == SBP_STAGE_Y_INVERSE) &&

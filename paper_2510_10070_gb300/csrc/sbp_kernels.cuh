@@ -97,6 +97,52 @@ struct ZArgs {
     const void* paper_tab;
 };
 
+// SASHA (Sect. 2.2): the k = 0 column in FP64 from the plane sums, one block.
+// vk0[i] = k0_coef Σ_j c_{i-j} (S_j - ρ̄ nx ny) + 4πG ρ̄ z_i (z_i/2 - centre·z0)
+// with ρ̄ = Σ S_j / N, z0 = Σ z_j S_j / Σ S_j (0 without mass) and c the k = 0
+// column of the periodic kernel -1/k_z² on the 2 nz padded grid.
+struct SashaArgs {
+    const double* tile_sums;  // [nz][tiles_per_plane]
+    int tiles_per_plane;
+    int nz;
+    const double* c00;        // [2 nz - 1]
+    double k0_coef;           // 4πG / (nx ny)
+    double fourpiG;           // 4πG
+    double cells_xy;          // nx ny
+    double Lz;                // cell centres z_i = -Lz/2 + (i + ½) Lz/nz
+    double centre;            // vertex of Φ0 in units of z0
+    double* vk0;              // [nz] out
+};
+
+// Block-wide sum of a pair of doubles (result in every thread); `tmp` holds
+// 2·(blockDim/32) doubles of shared memory.  Contains barriers.
+__device__ __forceinline__ double2 block_sum_d2(double2 v, double* tmp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = (blockDim.x + 31) / 32;
+    const int wl = min(32, (int)blockDim.x - warp * 32);
+    const unsigned mask = (wl == 32) ? 0xffffffffu : ((1u << wl) - 1u);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double a = __shfl_xor_sync(mask, v.x, o), b = __shfl_xor_sync(mask, v.y, o);
+        if ((lane ^ o) < wl) {
+            v.x += a;
+            v.y += b;
+        }
+    }
+    if (lane == 0) {
+        tmp[2 * warp] = v.x;
+        tmp[2 * warp + 1] = v.y;
+    }
+    __syncthreads();
+    double2 r = make_double2(0.0, 0.0);
+    for (int w = 0; w < nw; ++w) {
+        r.x += tmp[2 * w];
+        r.y += tmp[2 * w + 1];
+    }
+    __syncthreads();
+    return r;
+}
+
 // Block (0,0) of a z pass: the FP64 mean mode (O(nz²) FP64 work on one SM,
 // overlapped with the other blocks).  `scratch` holds nz doubles.
 __device__ __forceinline__ void mean_mode_fp64(const ZArgs& A, int nz, double* scratch) {
@@ -342,6 +388,15 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forw
             }
             const FF tot = block_sum_ff(acc);
             if (tid == 0) tile_sums[bid] = (double)tot.hi + (double)tot.lo;
+        }
+    } else {
+        if (tile_sums != nullptr) {  // FP64 plane sums (SASHA)
+            __shared__ double dsum[2 * (kMaxThreads / 32)];
+            double acc = 0.0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc += (double)v[0][e].x + (double)v[0][e].y;
+            const double2 tot = block_sum_d2(make_double2(acc, 0.0), dsum);
+            if (tid == 0) tile_sums[bid] = tot.x;
         }
     }
     __syncthreads();  // twiddles visible

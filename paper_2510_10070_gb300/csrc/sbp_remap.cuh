@@ -10,7 +10,7 @@
 //
 //   k_ry_forward   real y-columns (two per complex transform) → y half
 //                  spectrum, phase exp(-i K_y s x), FP64 Green's table blocks,
-//                  FP32 plane sums
+//                  plane sums for the FP64 mean mode (FP32 path, SASHA)
 //   k_rows_c2c     complex x-rows, forward
 //   z pass         unchanged (it reads the Green's table per stored mode)
 //   k_rows_c2c     complex x-rows, inverse
@@ -40,7 +40,7 @@ struct RArgs {
     double s;             // s = Δy0 / L_x
     const double* s_dev;  // if set, s is read from device memory (batched executor)
     double lx_over_ly;    // L_x / L_y
-    const double* vk0;    // FP32 mean mode per plane, added by k_ry_inverse (or null)
+    const double* vk0;    // FP64 mean mode per plane, added by k_ry_inverse (or null)
 };
 
 // Turn fraction u of column x (cell centre) as a fixed-point count.
@@ -132,6 +132,15 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
             }
             const FF tot = block_sum_ff(acc);
             if (tid == 0) tile_sums[bid] = (double)tot.hi + (double)tot.lo;
+        }
+    } else {
+        if (tile_sums != nullptr) {  // FP64 plane sums (SASHA)
+            __shared__ double dsum[2 * (kMaxThreads / 32)];
+            double acc = 0.0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc += (double)v[0][e].x + (double)v[0][e].y;
+            const double2 tot = block_sum_d2(make_double2(acc, 0.0), dsum);
+            if (tid == 0) tile_sums[bid] = tot.x;
         }
     }
     __syncthreads();  // twiddles visible

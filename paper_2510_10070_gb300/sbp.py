@@ -52,6 +52,7 @@ class Option(IntEnum):
     DEBUG_WITHHOLD_COPY = 5
     TRUNCATION = 6
     FRAME = 7
+    METHOD = 8
 
 
 class SbpError(RuntimeError):
