@@ -58,7 +58,7 @@ struct XArgs {
     int pitch;           // spectrum row pitch (complex elements)
     int C;               // row pairs per block (divides ny/2)
     int pairs_per_plane; // ny/2
-    // x forward: the first green_blocks blocks fill the Green's table (FP64)
+    // x forward: the first green_blocks blocks fill the Green's table
     // while the others transform rows
     int green_blocks;
     GreenFill gf;
@@ -276,6 +276,40 @@ __device__ __forceinline__ GreenMode green_mode(int a, int b, int nx, int ny, do
     return g;
 }
 
+// The same parameters in FP32 for the FP32 path: |k|² and expm1 to float
+// rounding (relative error about 1e-7, far inside the FP32 tolerance), at the
+// FP32 rate instead of GB300's 1/64-rate FP64 pipe.
+struct GreenModeF {
+    float k2a, omEa, k2b, omEb;
+    int kzero, same;
+};
+__device__ __forceinline__ GreenModeF green_mode_f(int a, int b, int nx, int ny, float kxs, float kys, float L,
+                                                   float s) {
+    GreenModeF g;
+    const int as = (a < nx / 2) ? a : a - nx;
+    const int bs = (b < ny / 2) ? b : b - ny;
+    const int ap = wrap_signed(-as, nx);
+    const int bp = wrap_signed(-bs, ny);
+    g.kzero = (as == 0 && bs == 0);
+    {
+        const float Kx = kxs * (float)as, Ky = kys * (float)bs;
+        const float kx = fmaf(s, Ky, Kx);
+        g.k2a = fmaf(kx, kx, Ky * Ky);
+        g.omEa = g.kzero ? 0.f : -expm1f(-sqrtf(g.k2a) * L);
+    }
+    g.same = (ap == -as && bp == -bs);
+    if (g.same) {
+        g.k2b = g.k2a;
+        g.omEb = g.omEa;
+    } else {
+        const float Kx = kxs * (float)ap, Ky = kys * (float)bp;
+        const float kx = fmaf(s, Ky, Kx);
+        g.k2b = fmaf(kx, kx, Ky * Ky);
+        g.omEb = -expm1f(-sqrtf(g.k2b) * L);
+    }
+    return g;
+}
+
 template <typename T>
 __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     if (gf.tab == nullptr) return;
@@ -285,10 +319,20 @@ __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     const int q0 = block * gf.per_block;
     const int q1 = min(total, q0 + gf.per_block);
     const double s = gf.s_dev != nullptr ? *gf.s_dev : gf.s;
-    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
-        const int b = q / h, a = q - b * h;
-        const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, s);
-        tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
+    if constexpr (sizeof(T) == 4) {
+        const float kxs = (float)(kTwoPi / gf.Lx), kys = (float)(kTwoPi / gf.Ly);
+        const float L = (float)gf.L, sf = (float)s;
+        for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+            const int b = q / h, a = q - b * h;
+            const GreenModeF g = green_mode_f(a, b, gf.nx, gf.ny, kxs, kys, L, sf);
+            tab[q] = GreenT<T>{g.k2a, g.omEa, g.k2b, g.omEb, g.kzero, g.same};
+        }
+    } else {
+        for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+            const int b = q / h, a = q - b * h;
+            const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, s);
+            tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
+        }
     }
 }
 
@@ -355,7 +399,7 @@ template <typename T, int E, int NS>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
                                                            const cpx<T>* __restrict__ twg,
                                                            double* __restrict__ tile_sums, XArgs A) {
-    if ((int)blockIdx.x < A.green_blocks) {  // FP64 Green's table, off the transform blocks
+    if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
         green_fill<T>(A.gf, blockIdx.x);
         return;
     }

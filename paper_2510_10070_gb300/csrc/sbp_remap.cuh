@@ -94,7 +94,7 @@ template <typename T, int E, int NY, int CP>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
     k_ry_forward(const T* __restrict__ rho, cpx<T>* __restrict__ V, const cpx<T>* __restrict__ twg,
                  double* __restrict__ tile_sums, RArgs A) {
-    if ((int)blockIdx.x < A.green_blocks) {  // FP64 Green's table, off the transform blocks
+    if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
         green_fill<T>(A.gf, blockIdx.x);
         return;
     }
