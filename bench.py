@@ -371,27 +371,47 @@ def main():
         from paper_2510_10070_gb300 import workloads as W
 
         rho256 = W.lognormal_disc(W.BOX_256, seed=2, sigma=0.5)
-        # alpha = 1.1 with 4·nz padding: the paper's own vertical truncation (Sect. 2.3)
-        for name, d, alpha in (("box256_fp64", 0, 1.0), ("box256_fp32", 1, 1.0),
-                               ("box256_fp64_alpha1.1_pad4", 0, 1.1), ("box256_fp32_alpha1.1_pad4", 1, 1.1)):
+        # the "next" rows on the same box: the paper's α = 1.1 with 4·nz padding
+        # (Sect. 2.3), the physical frame (Sect. 2.1 mapping fused into the y
+        # passes) and SASHA (Sect. 2.2); plus the force of Sect. 2.4's ghost rule
+        O = sbp.Option
+        cases = (("box256_fp64", 0, ()), ("box256_fp32", 1, ()),
+                 ("box256_fp64_alpha1.1_pad4", 0, ((O.TRUNCATION, 1.1),)),
+                 ("box256_fp32_alpha1.1_pad4", 1, ((O.TRUNCATION, 1.1),)),
+                 ("box256_fp32_physical_frame", 1, ((O.FRAME, 1),)),
+                 ("box256_fp32_sasha", 1, ((O.METHOD, 2),)),
+                 ("box256_fp32_force", 1, ("force",)))
+        for name, d, opts in cases:
             b = W.BOX_256
             p = sbp.Plan(b.nx, b.ny, b.nz, b.Lx, b.Ly, b.Lz, q=b.q, dtype=d)
-            if alpha != 1.0:
-                p.set_option(sbp.Option.TRUNCATION, alpha)
+            force = "force" in opts
+            for o in opts:
+                if o != "force":
+                    p.set_option(o[0], o[1])
             r = torch.from_numpy(rho256).to(device=dev, dtype=torch.float64 if d == 0 else torch.float32)
             f = torch.empty_like(r)
+            g = torch.empty((3,) + tuple(r.shape), dtype=r.dtype, device=dev) if force else None
+
+            def once():
+                if force:
+                    p.force(r, t=1.3, out=g, stream=stream)
+                else:
+                    p.solve(r, f, t=1.3, stream=stream)
             for _ in range(3):
-                p.solve(r, f, t=1.3, stream=stream)
+                once()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             reps = 5 if d == 0 else 20
             a0.record(stream)
             for _ in range(reps):
-                p.solve(r, f, t=1.3, stream=stream)
+                once()
             a1.record(stream)
             torch.cuda.synchronize()
             t_ms = a0.elapsed_time(a1) / reps
-            side[name] = {"ms_per_solve": t_ms, "solves_per_s": 1e3 / t_ms,
-                          "gcells_per_s": b.cells / (t_ms / 1e3) / 1e9}
+            if force:
+                side[name] = {"ms_per_call": t_ms, "gb_per_s": 4 * r.numel() * r.element_size() / (t_ms / 1e3) / 1e9}
+            else:
+                side[name] = {"ms_per_solve": t_ms, "solves_per_s": 1e3 / t_ms,
+                              "gcells_per_s": b.cells / (t_ms / 1e3) / 1e9}
         side["batch_fp32_vs_box256_fp64_cells_speedup"] = (cells / (ms_per_step / 1e3) / 1e9) / \
             side["box256_fp64"]["gcells_per_s"]
 

@@ -25,6 +25,9 @@ def main(argv=None):
     ap.add_argument("--z-variant", type=int, default=0)
     ap.add_argument("--xy-passes", type=int, default=0)
     ap.add_argument("--alpha", type=float, default=1.0, help="vertical truncation L/Lz (> 1: 4·nz padding)")
+    ap.add_argument("--frame", type=int, default=0, help="1: physical frame (Sect. 2.1 mapping)")
+    ap.add_argument("--method", type=int, default=0, help="1, 2: SASHA (Sect. 2.2)")
+    ap.add_argument("--force", action="store_true", help="also take -grad(phi) after each solve")
     args = ap.parse_args(argv)
     nx, ny, nz = (int(v) for v in args.box.lower().split("x"))
     Lx, Ly, Lz = (float(v) for v in args.lengths.split(","))
@@ -36,14 +39,21 @@ def main(argv=None):
         plan.set_option(sbp.Option.XY_PASSES, args.xy_passes)
     if args.alpha != 1.0:
         plan.set_option(sbp.Option.TRUNCATION, args.alpha)
+    if args.frame:
+        plan.set_option(sbp.Option.FRAME, args.frame)
+    if args.method:
+        plan.set_option(sbp.Option.METHOD, args.method)
     g = torch.Generator(device="cuda").manual_seed(1)
     z = (torch.arange(nz, device="cuda", dtype=torch.float64) + 0.5) * (Lz / nz) - 0.5 * Lz
     rho = torch.exp(-0.5 * z * z)[:, None, None] * (1.0 + 0.1 * torch.rand((nz, ny, nx), generator=g,
                                                                            device="cuda", dtype=torch.float64))
     rho = rho.to(plan.torch_dtype).contiguous()
     phi = torch.empty_like(rho)
+    g = torch.empty((3,) + tuple(rho.shape), dtype=rho.dtype, device="cuda") if args.force else None
     for _ in range(args.solves):
         plan.solve(rho, phi, t=args.t)
+        if g is not None:
+            plan.force(phi, t=args.t, out=g)
     torch.cuda.synchronize()
     print(f"{args.solves} solves of {nx}x{ny}x{nz} ({args.dtype}) done")
 
