@@ -28,6 +28,10 @@ template <typename T, int E>
 constexpr int min_blocks_xy() { return (sizeof(T) == 8 || E > 16) ? 2 : 4; }
 template <typename T, int E>
 constexpr int min_blocks_z() { return (sizeof(T) == 8 || E > 16) ? 2 : 3; }
+// The padded z kernel fits 64 registers at E = 16 (its radix-16 stages apply
+// their twiddles one first-level group at a time), so four blocks per SM.
+template <typename T, int E>
+constexpr int min_blocks_zpad() { return (sizeof(T) == 8 || E > 16) ? 2 : 4; }
 
 // Row stride (complex elements) of a [n][C] exchange buffer: one pad column
 // spreads consecutive rows over the banks; a single column needs none.
@@ -779,7 +783,7 @@ __device__ __forceinline__ T green_factor(const GreenCoef<T>& q, int m, int ms, 
 // is stored, so the compiler drops the rest of the last stage.
 // smem: twM[M] | green[C] | exchange of C columns of M (XchgCol)
 template <typename T, int E, int N>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_zpad<T, E>())) k_z_padded(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ /*unused*/,
                                                           const cpx<T>* __restrict__ twMg, const T* __restrict__ /*unused*/,
                                                           ZArgs A) {
     constexpr int M = 2 * N;
