@@ -191,7 +191,16 @@ enum {
      * from the box centre.  Requires SBP_OPT_TRUNCATION = 1 (else
      * SBP_ERR_UNSUPPORTED_SIZE, either order); sbp_run_stage returns
      * SBP_ERR_INVALID_ARG while it is not 0. */
-    SBP_OPT_METHOD = 8
+    SBP_OPT_METHOD = 8,
+    /* Planes per chunk of the x and y passes of sbp_solve (0, the default: the
+     * whole box at once).  With chunks, the forward x and y passes run chunk
+     * by chunk, and so do the inverse ones, so that a chunk's half spectrum is
+     * still in L2 when the next pass reads it; fewer blocks per launch, so it
+     * pays when several solves share the GPU.  sbp_solve_batched chooses by
+     * itself: its first call times the graphs with and without chunks of
+     * about 8 MiB of spectrum (SBP_BATCH_CHUNK=0/1 in the environment forces
+     * one).  Results are identical either way. */
+    SBP_OPT_XY_CHUNK = 9
 };
 
 /* sbp_fill_ghosts — vertical ghost layers of a solution (Sect. 2.4, last

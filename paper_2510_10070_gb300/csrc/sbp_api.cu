@@ -98,6 +98,7 @@ struct sbp_plan_s {
     // method (SBP_OPT_METHOD): 0 = VGF-HybridBC, 1 = SASHA with Φ0's vertex at z0
     // (as printed), 2 = SASHA with the vertex at z0/2
     int method = 0;
+    int chunk = 0;  // planes per x/y chunk of a single solve (SBP_OPT_XY_CHUNK; 0: whole box)
     // z-pass geometry: stored columns per row, rows per plane, row pitch
     int zh = 0, zrows = 0, zpitch = 0;
     // physical frame (SBP_OPT_FRAME = 1): y-first passes with the mapping of Sect. 2.1
@@ -727,6 +728,7 @@ YArgs make_yargs(const sbp_plan_s* p) {
     a.pitch = p->pitch;
     a.h = p->h;
     a.C = p->yp.C;
+    a.z0 = 0;
     return a;
 }
 template <typename T>
@@ -759,23 +761,37 @@ ZArgs make_zargs(const sbp_plan_s* p, bool with_k0) {
 // and the x inverse pass adds the FP64 mean mode.  Run alone, a stage does
 // only its own transform; the z pass then fills its table first.
 template <typename T>
+// z0, nzc: the x and y stages may run on planes [z0, z0 + nzc) only (a chunk
+// of the box, see solve_t); nzc < 0 means the whole box.
 sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, double t, cudaStream_t st,
-                        bool fused, const double* s_dev = nullptr) {
+                        bool fused, const double* s_dev = nullptr, int z0 = 0, int nzc = -1) {
     const KernelSet<T> kx = kernels_for<T>(p->nx, p->px.E), ky = kernels_for<T>(p->ny, p->py.E);
     const bool f32 = !f64_of(p);
     cpx<T>* W = static_cast<cpx<T>*>(out);
+    if (nzc < 0) {
+        z0 = 0;
+        nzc = p->nz;
+    }
+    const size_t plane_re = (size_t)p->nx * p->ny, plane_sp = (size_t)p->ny * p->pitch;
+    const int x_blocks = (int)((long long)nzc * (p->ny / 2) / p->xf.C);  // row-pair blocks of the chunk
+    YArgs ya = make_yargs<T>(p);
+    ya.z0 = z0;
+    const dim3 ygrid(p->yp.grid.x, (unsigned)nzc, 1);
     switch (stage) {
         case SBP_STAGE_X_FORWARD: {
             XArgs a = make_xargs<T>(p);
             dim3 grid = p->xf.grid;
-            if (fused) {
+            grid.x = (unsigned)x_blocks;
+            if (fused && z0 == 0) {  // the whole Green's table, with the first chunk
                 a.green_blocks = p->green_blocks;
                 a.gf = make_green_fill(p, t, p->green_blocks);
                 a.gf.s_dev = s_dev;
                 grid.x += p->green_blocks;
             }
             double* sums = ((f32 || p->method != 0) && fused) ? p->tile_sums : nullptr;
-            kx.x_fwd<<<grid, p->xf.threads, p->xf.smem, st>>>(static_cast<const T*>(in), W,
+            if (sums) sums += (size_t)z0 * (p->ny / 2) / p->xf.C;
+            kx.x_fwd<<<grid, p->xf.threads, p->xf.smem, st>>>(static_cast<const T*>(in) + z0 * plane_re,
+                                                             W + z0 * plane_sp,
                                                              static_cast<const cpx<T>*>(p->tw_x), sums, a);
             break;
         }
@@ -788,11 +804,10 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
                     if (!encode_ymap<T>(p, out, &local)) return SBP_ERR_INVALID_ARG;
                     map = &local;
                 }
-                ky.y_fwd_tma<<<p->yp.grid, p->yp.threads, p->y_tma_smem, st>>>(
-                    W, static_cast<const cpx<T>*>(p->tw_y), make_yargs<T>(p), make_tmactl(p), *map);
+                ky.y_fwd_tma<<<ygrid, p->yp.threads, p->y_tma_smem, st>>>(
+                    W, static_cast<const cpx<T>*>(p->tw_y), ya, make_tmactl(p), *map);
             } else {
-                ky.y_fwd<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
-                                                                       make_yargs<T>(p));
+                ky.y_fwd<<<ygrid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y), ya);
             }
             break;
         case SBP_STAGE_GREEN_FILL: {
@@ -819,18 +834,18 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
                     if (!encode_ymap<T>(p, out, &local)) return SBP_ERR_INVALID_ARG;
                     map = &local;
                 }
-                ky.y_inv_tma<<<p->yp.grid, p->yp.threads, p->y_tma_smem, st>>>(
-                    W, static_cast<const cpx<T>*>(p->tw_y), make_yargs<T>(p), make_tmactl(p), *map);
+                ky.y_inv_tma<<<ygrid, p->yp.threads, p->y_tma_smem, st>>>(
+                    W, static_cast<const cpx<T>*>(p->tw_y), ya, make_tmactl(p), *map);
             } else {
-                ky.y_inv<<<p->yp.grid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y),
-                                                                       make_yargs<T>(p));
+                ky.y_inv<<<ygrid, p->yp.threads, p->yp.smem, st>>>(W, static_cast<const cpx<T>*>(p->tw_y), ya);
             }
             break;
         case SBP_STAGE_X_INVERSE: {
             XArgs a = make_xargs<T>(p);
-            if ((f32 || p->method != 0) && fused) a.vk0 = p->vk0;
-            kx.x_inv<<<p->xi.grid, p->xi.threads, p->xi.smem, st>>>(
-                static_cast<const cpx<T>*>(in), static_cast<T*>(out), static_cast<const cpx<T>*>(p->tw_x), a);
+            if ((f32 || p->method != 0) && fused) a.vk0 = p->vk0 + z0;
+            kx.x_inv<<<dim3((unsigned)x_blocks), p->xi.threads, p->xi.smem, st>>>(
+                static_cast<const cpx<T>*>(in) + z0 * plane_sp, static_cast<T*>(out) + z0 * plane_re,
+                static_cast<const cpx<T>*>(p->tw_x), a);
             break;
         }
         case SBP_STAGE_GREEN_TABLE: {
@@ -1007,10 +1022,31 @@ bool configure_frame(sbp_plan_s* p, int frame) {
 
 template <typename T>
 sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
-                   const double* s_dev = nullptr) {
+                   const double* s_dev = nullptr, int chunk = -1) {
     if (p->frame) return solve_physical_t<T>(p, rho, phi, t, st, s_dev);
     if (p->xy_fused) return solve_fused_t<T>(p, rho, phi, t, st, s_dev);
+    if (chunk < 0) chunk = p->chunk;
     sbp_status s;
+    if (chunk > 0 && chunk < p->nz) {
+        // x and y passes chunk by chunk, so that a chunk's half spectrum is
+        // still in L2 when the next pass reads it (SBP_OPT_XY_CHUNK)
+        for (int z0 = 0; z0 < p->nz; z0 += chunk) {
+            const int n = std::min(chunk, p->nz - z0);
+            if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true, s_dev, z0, n)) != SBP_OK)
+                return s;
+            if ((s = launch_stage<T>(p, SBP_STAGE_Y_FORWARD, p->W, p->W, t, st, true, nullptr, z0, n)) != SBP_OK)
+                return s;
+        }
+        if ((s = launch_stage<T>(p, SBP_STAGE_Z_CONVOLVE, p->W, p->W, t, st, true)) != SBP_OK) return s;
+        for (int z0 = 0; z0 < p->nz; z0 += chunk) {
+            const int n = std::min(chunk, p->nz - z0);
+            if ((s = launch_stage<T>(p, SBP_STAGE_Y_INVERSE, p->W, p->W, t, st, true, nullptr, z0, n)) != SBP_OK)
+                return s;
+            if ((s = launch_stage<T>(p, SBP_STAGE_X_INVERSE, p->W, phi, t, st, true, nullptr, z0, n)) != SBP_OK)
+                return s;
+        }
+        return SBP_OK;
+    }
     if ((s = launch_stage<T>(p, SBP_STAGE_X_FORWARD, rho, p->W, t, st, true, s_dev)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Y_FORWARD, p->W, p->W, t, st, true)) != SBP_OK) return s;
     if ((s = launch_stage<T>(p, SBP_STAGE_Z_CONVOLVE, p->W, p->W, t, st, true)) != SBP_OK) return s;
@@ -1048,6 +1084,7 @@ struct BatchExec {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int branches = 0;
+    int chunked = 0;  // the boxes' x/y passes run in chunks (auto_chunk)
     float tuned_ms = 0.f;
 };
 
@@ -1078,7 +1115,16 @@ void drop_executors(const sbp_plan_s* p) {
     }
 }
 
-sbp_status capture_batch(BatchExec* e, int K, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
+// Planes per x/y chunk that keep a chunk's half spectrum near 8 MiB (0 when
+// the whole box is already that small or the plan takes other passes).
+int auto_chunk(const sbp_plan_s* p) {
+    if (p->frame || p->xy_fused) return 0;
+    const size_t plane = (size_t)p->ny * p->pitch * 2 * p->rsize;
+    const int c = (int)std::max<size_t>(1, ((size_t)8 << 20) / plane);
+    return c >= p->nz ? 0 : c;
+}
+
+sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
     const int n = (int)e->plans.size();
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> br(K, nullptr);
@@ -1108,8 +1154,10 @@ sbp_status capture_batch(BatchExec* e, int K, cudaGraph_t* graph_out, cudaGraphE
             const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
             sbp_plan_s* p = e->plans[i];
             load[k] += (double)p->nx * p->ny * p->nz;
-            const sbp_status s = f64_of(p) ? solve_t<double>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i)
-                                           : solve_t<float>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i);
+            const int chunk = chunked ? auto_chunk(p) : 0;
+            const sbp_status s = f64_of(p)
+                                     ? solve_t<double>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, chunk)
+                                     : solve_t<float>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, chunk);
             if (s != SBP_OK && st == SBP_OK) st = s;
         }
         for (int k = 0; k < K; ++k) {
@@ -1149,22 +1197,37 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
         for (int k : {1, 2, 4, 8, 16, 32})
             if (k <= std::max(1, n)) cands.push_back(k);
     cudaEvent_t a = nullptr, b = nullptr;
-    if (cands.size() > 1 && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)) {
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         cudaGetLastError();
         return SBP_ERR_CUDA;
     }
+    // chunked x/y passes only where some box has more than one chunk
+    std::vector<int> chunk_modes = {0};
+    if (const char* env = std::getenv("SBP_BATCH_CHUNK")) {
+        chunk_modes = {std::atoi(env) != 0 ? 1 : 0};
+    } else {
+        for (const sbp_plan_s* p : e->plans)
+            if (auto_chunk(p) > 0) {
+                chunk_modes.push_back(1);
+                break;
+            }
+    }
+    std::vector<std::pair<int, int>> trials;
+    for (int K : cands)
+        for (int c : chunk_modes) trials.push_back({K, c});
     float best = 0.f;
-    for (int K : cands) {
+    for (const auto& tr : trials) {
+        const int K = tr.first;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
-        const sbp_status s = capture_batch(e, K, &g, &x);
+        const sbp_status s = capture_batch(e, K, tr.second != 0, &g, &x);
         if (s != SBP_OK) {
             if (a) cudaEventDestroy(a);
             if (b) cudaEventDestroy(b);
             return s;
         }
         float ms = 0.f;
-        if (cands.size() > 1) {
+        if (trials.size() > 1) {
             cudaGraphLaunch(x, st);
             cudaEventRecord(a, st);
             for (int r = 0; r < 3; ++r) cudaGraphLaunch(x, st);
@@ -1184,6 +1247,7 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
             e->exec = x;
             e->graph = g;
             e->branches = K;
+            e->chunked = tr.second;
             best = ms;
         } else {
             cudaGraphExecDestroy(x);
@@ -1479,6 +1543,12 @@ sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
         if (!g.ok) return SBP_ERR_CUDA;
         const bool ok = f64_of(p) ? configure_frame<double>(p, (int)value) : configure_frame<float>(p, (int)value);
         return ok ? SBP_OK : SBP_ERR_UNSUPPORTED_SIZE;
+    }
+    if (option == SBP_OPT_XY_CHUNK) {
+        const int v = (int)value;
+        if ((double)v != value || v < 0) return SBP_ERR_INVALID_ARG;
+        p->chunk = v;
+        return SBP_OK;
     }
     if (option == SBP_OPT_METHOD) {
         const int v = (int)value;

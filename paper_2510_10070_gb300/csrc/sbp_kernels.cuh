@@ -75,6 +75,7 @@ struct YArgs {
     int pitch;
     int h;      // nx/2 + 1
     int C;      // columns per block
+    int z0;     // first plane of this launch (grid.y planes from there)
 };
 
 struct ZArgs {
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass
     const int a = blockIdx.x * C + c;
     const bool valid = a < A.h;
     const size_t step = (size_t)Tf * A.pitch;
-    cpx<T>* col = W + ((size_t)blockIdx.y * n + t) * A.pitch + a;
+    cpx<T>* col = W + (((size_t)blockIdx.y + A.z0) * n + t) * A.pitch + a;
     cpx<T> v[1][E];
     {
         const cpx<T>* src = col;
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
     uint64_t* bar = reinterpret_cast<uint64_t*>(tw + NS);
     const int tid = threadIdx.x;
     const int a0 = blockIdx.x * C;
-    const int row0 = blockIdx.y * NS;
+    const int row0 = (blockIdx.y + A.z0) * NS;
     if (tid == 0) {
         mbar_init(bar, 1);
         mbar_fence_init();

@@ -243,6 +243,7 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     ya.pitch = pitch;
     ya.h = h;
     ya.C = Cy;
+    ya.z0 = 0;
     const dim3 ygrid((h + Cy - 1) / Cy, nz);
     const cpx<float>* twy = reinterpret_cast<const cpx<float>*>(base + oTy);
     ky.y_fwd<<<ygrid, Cy * py.Tf, ysm(Cy), st>>>(W, twy, ya);

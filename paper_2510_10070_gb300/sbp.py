@@ -53,6 +53,7 @@ class Option(IntEnum):
     TRUNCATION = 6
     FRAME = 7
     METHOD = 8
+    XY_CHUNK = 9
 
 
 class SbpError(RuntimeError):

@@ -247,3 +247,44 @@ def test_box1024_clumpy_fp32_against_fp64(sbp):
     got = p32.solve(rho.float(), t=W.T_1024)
     err = (torch.linalg.vector_norm((got.double() - ref).ravel()) / torch.linalg.vector_norm(ref.ravel())).item()
     assert err <= TOL[1], err
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("shape,chunk", [((96, 64, 48), 7), ((128, 32, 24), 8), ((48, 24, 12), 5), ((256, 16, 8), 3)])
+def test_chunked_xy_passes_are_identical(sbp, shape, chunk, dtype):
+    # the x and y passes chunk by chunk (SBP_OPT_XY_CHUNK) change only the
+    # launch schedule: identical bits, VGF and SASHA (plane sums per chunk)
+    import torch
+
+    nx, ny, nz = shape
+    box = W.Box(nx, ny, nz, 2.0, 3.0, 1.5, q=1.5)
+    rng = np.random.default_rng(nx + nz)
+    rho = to_dev(rng.standard_normal((nz, ny, nx)) + 0.2, dtype)
+    for method in (0, 2):
+        whole = _plan(sbp, box, dtype)
+        parts = _plan(sbp, box, dtype)
+        whole.set_option(sbp.Option.XY_PASSES, 1)
+        parts.set_option(sbp.Option.XY_PASSES, 1)
+        whole.set_option(sbp.Option.METHOD, method)
+        parts.set_option(sbp.Option.METHOD, method)
+        parts.set_option(sbp.Option.XY_CHUNK, chunk)
+        a = whole.solve(rho, t=0.9)
+        b = parts.solve(rho, t=0.9)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), method
+
+
+def test_batched_with_chunks_matches_single(sbp, monkeypatch):
+    import torch
+
+    monkeypatch.setenv("SBP_BATCH_CHUNK", "1")
+    boxes = [W.Box(256, 256, 128, 8.0, 8.0, 4.0), W.Box(128, 128, 64, 8.0, 8.0, 4.0, q=1.0)]
+    rng = np.random.default_rng(12)
+    plans = [_plan(sbp, b, 1) for b in boxes]
+    rhos = [to_dev(rng.standard_normal((b.nz, b.ny, b.nx)), 1) for b in boxes]
+    outs = [torch.empty_like(r) for r in rhos]
+    ts = [1.1, 4.2]
+    sbp.solve_batched(plans, rhos, outs, ts)
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert torch.equal(outs[i], plans[i].solve(rhos[i], t=ts[i]))
