@@ -65,9 +65,10 @@ def build_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def recorded_traffic(kernel_name):
+def recorded_traffic(kernel_name, key=None):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    record, or None when the kernel sources changed since it was taken."""
+    record (or the record's field `key`), or None when the kernel sources
+    changed since it was taken."""
     import hashlib
 
     try:
@@ -81,7 +82,22 @@ def recorded_traffic(kernel_name):
         return None
     if rec.get("source_sha256") != h.hexdigest() or rec.get("kernel") != kernel_name:
         return None
+    if key is not None:
+        return rec.get(key)
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def issue_view(warp_instr, ms, dev, peaks):
+    if not warp_instr:
+        return None
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = sms * 4 * mhz * 1e6 / 1e9  # G warp-instructions/s
+    achieved = warp_instr / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gwarp-instr/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": warp_instr, "peak_source": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz"}
 
 
 def alg_bytes(box, rb):
@@ -408,6 +424,11 @@ def main():
                 "traffic": recorded_traffic(zname), "alg_bytes_per_launch": zbytes,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "step_alg_gbs": balg / (ms_per_step / 1e3) / 1e9,
+                # the z pass is bound by instruction issue, not HBM: the same
+                # launch against the SMs' issue rate (4 schedulers per SM, one
+                # warp instruction each per clock at the measured max clock),
+                # with the warp instructions counted by ncu for this launch
+                "issue_view": issue_view(recorded_traffic(zname, "warp_instructions"), z_ms, dev, peaks),
                 "step_frac": balg / (ms_per_step / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
     # FP64 and FP32 single-box reference numbers (the "vs FP64" of the metric)
