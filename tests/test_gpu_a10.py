@@ -1,0 +1,26 @@
+"""Accuracy of the tensor-core radix-16 measurement (the a10 option).
+
+16-point DFTs on the tensor cores with operands split hi/lo in FP16 must land
+within the FP32 bar after the split recovery (rel-L2 ≤ 2e-5) and within 1e-3
+with the hi·hi product alone; the engine's FP32 butterfly is the reference
+point.  The timings of the same run are what decides whether the option pays.
+"""
+
+import shutil
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_dft16_tensor_core_split_accuracy():
+    if shutil.which("nvcc") is None and not __import__("os").path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2510_10070_gb300.a10 import run
+
+    r = run.run(blocks=152, reps=8)
+    assert r["status"] == "no error"
+    assert r["cc_reg"]["rel_l2"] < 1e-6
+    assert r["cc_smem"]["rel_l2"] < 1e-6
+    assert r["mma3"]["rel_l2"] < 2e-5
+    assert r["mma1"]["rel_l2"] < 1e-3
