@@ -1,11 +1,13 @@
 // sbp_xy.cuh — fused x and y passes: one z-plane per thread-block cluster.
 //
 // Forward: each CTA of a cluster of CL transforms N/CL rows of the plane
-// along x (row pairs, as k_x_forward) into its own shared memory, the
-// cluster synchronises, and each CTA then transforms its share of the nx/2+1
-// half-spectrum columns along y, reading the other CTAs' rows through
-// distributed shared memory, and writes the spectrum.  The inverse runs the
-// same two phases in the opposite order.  The half spectrum of a plane goes
+// along x (row pairs, as k_x_forward) and stores every result straight into
+// the shared memory of the CTA that owns its column (distributed shared
+// memory stores, which do not wait); the cluster synchronises, and each CTA
+// then transforms its share of the nx/2+1 half-spectrum columns along y from
+// its own shared memory and writes the spectrum.  The inverse runs the same
+// two phases in the opposite order, pushing each y-transformed element to the
+// CTA that owns its row.  The half spectrum of a plane goes
 // through HBM once per direction instead of twice.
 #pragma once
 
@@ -48,8 +50,8 @@ struct XYShape {
     static constexpr int CY = CX;                              // columns per round
     static constexpr int ACOLS = (H + CL - 1) / CL;            // columns per CTA
     static constexpr int RP = padded_row(N);
-    static constexpr int S_FWD = ROWS * H;                     // forward: own rows, all columns
-    static constexpr int S_INV = N * ACOLS;                    // inverse: all rows, own columns
+    static constexpr int S_FWD = N * ACOLS;                    // forward: all rows, own columns
+    static constexpr int S_INV = ROWS * H;                     // inverse: own rows, all columns
     static constexpr int XBUF = cmax(CX * RP, N * xstride(CY));
     static constexpr size_t smem_fwd = (size_t)(S_FWD + N + XBUF) * sizeof(cpx<T>);
     static constexpr size_t smem_inv = (size_t)(S_INV + N + XBUF) * sizeof(cpx<T>);
@@ -82,14 +84,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
     const int rank = (int)cluster.block_rank();
     const int plane = ((int)blockIdx.x - A.green_ctas) / CL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);  // [ROWS][H]
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);  // [N][ACOLS]: all rows, own columns
     cpx<T>* tw = S + SH::S_FWD;
     cpx<T>* xb = tw + N;
     const int tid = threadIdx.x;
     for (int i = tid; i < N; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
+    cpx<T>* dst[CL];
+#pragma unroll
+    for (int r = 0; r < CL; ++r) dst[r] = cluster.map_shared_rank(S, r);
+    cluster.sync();  // every CTA has started before any writes into it; twiddles visible
 
-    // ---- phase 1: x transforms of this CTA's row pairs into S
+    // ---- phase 1: x transforms of this CTA's row pairs, pushed to the column owners
     FF acc = {0.f, 0.f};
     {
         const int t = tid % TF, c = tid / TF;
@@ -119,9 +124,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
                 const cpx<T> Az = zr[k + (k >> 4)];
                 const int km = (k == 0) ? 0 : N - k;
                 const cpx<T> Bz = cconj(zr[km + (km >> 4)]);
-                const int lr = 2 * (p0 + cc);
-                S[lr * H + k] = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
-                S[(lr + 1) * H + k] = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
+                const int y = rank * SH::ROWS + 2 * (p0 + cc);
+                const int owner = k / SH::ACOLS, ka = k - owner * SH::ACOLS;
+                cpx<T>* o = dst[owner] + (size_t)y * SH::ACOLS + ka;
+                o[0] = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
+                o[SH::ACOLS] = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
             }
             // the next round's first exchange write is preceded by a barrier
         }
@@ -146,15 +153,12 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
             }
         }
     }
-    cluster.sync();  // every CTA's rows are in its shared memory
+    cluster.sync();  // every CTA's columns are in its shared memory
 
-    // ---- phase 2: y transforms of this CTA's columns, rows from the cluster
+    // ---- phase 2: y transforms of this CTA's columns, from its own shared memory
     {
         const int c = tid % SH::CY, t = tid / SH::CY;
         const int a_begin = rank * SH::ACOLS, a_end = cmin(H, a_begin + SH::ACOLS);
-        const cpx<T>* rows[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) rows[r] = cluster.map_shared_rank(S, r);
         cpx<T>* wplane = W + (size_t)plane * N * A.pitch;
         for (int a0 = a_begin; a0 < a_end; a0 += SH::CY) {
             const int a = a0 + c;
@@ -163,8 +167,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int y = t + TF * e;
-                const int owner = y / SH::ROWS;
-                v[0][e] = valid ? rows[owner][(y - owner * SH::ROWS) * H + a] : cpx<T>{(T)0, (T)0};
+                v[0][e] = valid ? S[(size_t)y * SH::ACOLS + (a - a_begin)] : cpx<T>{(T)0, (T)0};
             }
             const SmemCol<T, xstride(SH::CY)> buf[1] = {{xb + c, 0}};
             fft_static<N, E, 0, 1, T>(v, t, tw, buf);
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_forward(const T* __restrict_
             }
         }
     }
-    cluster.sync();  // no CTA leaves while others may still read its rows
+    cluster.sync();  // no CTA leaves before the others' pushes into it are consumed
 }
 
 template <typename T, int N, int CL>
@@ -187,14 +190,17 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_inverse(const cpx<T>* __rest
     const int rank = (int)cluster.block_rank();
     const int plane = (int)blockIdx.x / CL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);  // [N][ACOLS]: all rows, own columns
+    cpx<T>* S = reinterpret_cast<cpx<T>*>(smem_raw);  // [ROWS][H]: own rows, all columns
     cpx<T>* tw = S + SH::S_INV;
     cpx<T>* xb = tw + N;
     const int tid = threadIdx.x;
     for (int i = tid; i < N; i += blockDim.x) tw[i] = twg[i];
-    __syncthreads();
+    cpx<T>* dst[CL];
+#pragma unroll
+    for (int r = 0; r < CL; ++r) dst[r] = cluster.map_shared_rank(S, r);
+    cluster.sync();  // every CTA has started before any writes into it; twiddles visible
 
-    // ---- phase 1: y inverse of this CTA's columns into S
+    // ---- phase 1: y inverse of this CTA's columns, pushed to the row owners
     const int a_begin = rank * AC, a_end = cmin(H, a_begin + AC);
     {
         const int c = tid % SH::CY, t = tid / SH::CY;
@@ -213,17 +219,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_inverse(const cpx<T>* __rest
             fft_static<N, E, 0, 1, T>(v, t, tw, buf);
             if (valid) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) S[(t + TF * e) * AC + (a - a_begin)] = cconj(v[0][e]);
+                for (int e = 0; e < E; ++e) {
+                    const int y = t + TF * e;
+                    const int owner = y / SH::ROWS;
+                    dst[owner][(size_t)(y - owner * SH::ROWS) * H + a] = cconj(v[0][e]);
+                }
             }
         }
     }
-    cluster.sync();  // every CTA's columns are in its shared memory
+    cluster.sync();  // every CTA's rows are in its shared memory
 
-    // ---- phase 2: x inverse of this CTA's row pairs, columns from the cluster
+    // ---- phase 2: x inverse of this CTA's row pairs, from its own shared memory
     {
-        const cpx<T>* cols[CL];
-#pragma unroll
-        for (int r = 0; r < CL; ++r) cols[r] = cluster.map_shared_rank(S, r);
         T add_hi = (T)0, add_lo = (T)0;
         const bool addk0 = (A.vk0 != nullptr);
         if (addk0) {
@@ -234,14 +241,13 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_inverse(const cpx<T>* __rest
         const int t = tid % TF, c = tid / TF;
         for (int p0 = 0; p0 < SH::PAIRS; p0 += SH::CX) {
             const int y0 = rank * SH::ROWS + 2 * (p0 + c);
+            const int yl = 2 * (p0 + c);  // local row
             cpx<T> v[1][E];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int k = t + TF * e;
                 const int kk = (2 * k <= N) ? k : N - k;
-                const int owner = kk / AC;
-                const cpx<T>* src = cols[owner] + (kk - owner * AC);
-                cpx<T> x0 = src[y0 * AC], x1 = src[(y0 + 1) * AC];
+                cpx<T> x0 = S[(size_t)yl * H + kk], x1 = S[(size_t)(yl + 1) * H + kk];
                 cpx<T> z;
                 if (2 * k <= N) {
                     if (k == 0 || 2 * k == N) {
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_xy_inverse(const cpx<T>* __rest
             }
         }
     }
-    cluster.sync();  // no CTA leaves while others may still read its columns
+    cluster.sync();  // keeps the cluster together to the end, as in the forward kernel
 }
 
 }  // namespace sbp
