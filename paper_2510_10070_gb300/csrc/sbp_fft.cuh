@@ -36,6 +36,32 @@ template <typename T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
     return {fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x)};
 }
+// FP32 complex add and subtract as one packed f32x2 instruction (sm_100
+// family): the same round-to-nearest results as two scalar FADDs in half the
+// issue slots.  The butterflies are mostly complex adds, so this is where
+// the transforms spend most of their instructions.
+__device__ __forceinline__ cpx<float> cadd(cpx<float> a, cpx<float> b) {
+    cpx<float> r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "add.rn.f32x2 pr, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ cpx<float> csub(cpx<float> a, cpx<float> b) {
+    cpx<float> r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.f32x2 pr, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 template <typename T>
 __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
 template <typename T>
