@@ -451,14 +451,48 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forw
     __syncthreads();  // twiddles visible
     const SmemRow<T> buf[1] = {{xb + c * RP, 0}};
     fft_run<NS, E, 1, T>(v, t, A.P, tw, buf);
+
+    // split the paired transform: X0 = (Z[k] + conj Z[n-k]) / 2, X1 = -i (Z[k] - conj Z[n-k]) / 2
+    const T half = (T)0.5;
+    if constexpr (NS > 0 && NS / E <= 32) {
+        // Static plans whose row pair fits in one warp: Z[n-k] is in a lane of
+        // the same row pair (k = t + Tf·e: element E-1-e of lane Tf-t for
+        // t > 0, element (E-e) mod E of lane t = 0 itself), so the split runs
+        // on warp shuffles instead of a shared-memory round trip.  Tf is a
+        // power of two and row pairs never straddle a warp.
+        constexpr int TF = NS / E;
+        static_assert((TF & (TF - 1)) == 0, "row-pair lane groups must tile a warp");
+        const int lane = tid & 31;
+        const int src = lane - t + ((TF - t) & (TF - 1));
+        const int live = min(32, (int)blockDim.x - (tid & ~31));
+        const unsigned mask = live == 32 ? 0xffffffffu : ((1u << live) - 1u);
+        const long long row = 2 * (pair0 + c);
+        cpx<T>* o0 = W + row * A.pitch;
+        cpx<T>* o1 = o0 + A.pitch;
+#pragma unroll
+        for (int e = 0; e <= E / 2; ++e) {
+            const cpx<T> send = v[0][E - 1 - e];
+            cpx<T> Bz;
+            Bz.x = __shfl_sync(mask, send.x, src);
+            Bz.y = __shfl_sync(mask, send.y, src);
+            if (t == 0) Bz = v[0][(E - e) % E];
+            Bz = cconj(Bz);
+            const cpx<T> Az = v[0][e];
+            const cpx<T> X0 = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
+            const cpx<T> X1 = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
+            if (e < E / 2 || t == 0) {
+                const int k = t + TF * e;
+                o0[k] = X0;
+                o1[k] = X1;
+            }
+        }
+        return;
+    }
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < E; ++e) buf[0][t + Tf * e] = v[0][e];
     __syncthreads();
-
-    // split the paired transform: X0 = (Z[k] + conj Z[n-k]) / 2, X1 = -i (Z[k] - conj Z[n-k]) / 2
     const int h = n / 2 + 1;
-    const T half = (T)0.5;
     for (int q = tid; q < C * h; q += blockDim.x) {
         const int cc = q / h, k = q - cc * h;
         const cpx<T>* zr = xb + cc * RP;
