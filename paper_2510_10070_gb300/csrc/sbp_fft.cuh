@@ -64,6 +64,20 @@ __device__ __forceinline__ cpx<float> csub(cpx<float> a, cpx<float> b) {
 }
 template <typename T>
 __device__ __forceinline__ cpx<T> cconj(cpx<T> a) { return {a.x, -a.y}; }
+// conj(a)·f for real f; FP32 as one packed multiply by (f, -f).
+template <typename T>
+__device__ __forceinline__ cpx<T> cconj_scale(cpx<T> a, T f) { return {a.x * f, -a.y * f}; }
+__device__ __forceinline__ cpx<float> cconj_scale(cpx<float> a, float f) {
+    cpx<float> r;
+    asm("{\n\t.reg .b64 pa, pf, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pf, {%4, %5};\n\t"
+        "mul.rn.f32x2 pr, pa, pf;\n\t"
+        "mov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(f), "f"(-f));
+    return r;
+}
 template <typename T>
 __device__ __forceinline__ cpx<T> cscale(cpx<T> a, T s) { return {a.x * s, a.y * s}; }
 // a·(-i)

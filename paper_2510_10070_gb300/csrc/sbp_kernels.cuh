@@ -871,12 +871,14 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_zpad<T, E>())) k_z_pa
         if (__all_sync(0xffffffffu, q.same && !q.kzero)) {
             // the common case, uniform across the warp: one screened term
             const T num = (t & 1) ? q.ao : q.ae;
+            const T tf = (T)t;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int m = t + Tf * e;
-                const int ms = (m <= N) ? m : M - m;  // |signed m|
-                const T f = fast_div(num, q.k2a + kzc * (T)(ms * ms));
-                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+                // |signed m| of m = t + Tf·e: m itself below the Nyquist index
+                // (e < E/2), M - m from there on; exact small integers in T
+                const T ms = (e < E / 2) ? tf + (T)(Tf * e) : (T)(M - Tf * e) - tf;
+                const T f = fast_div(num, fma(kzc * ms, ms, q.k2a));
+                v[0][e] = cconj_scale(v[0][e], f);
             }
         } else {
 #pragma unroll
