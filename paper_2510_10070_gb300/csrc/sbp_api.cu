@@ -1185,9 +1185,26 @@ sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_o
     return SBP_OK;
 }
 
-// Build the executor's graph, choosing K by timing when not forced.
+// Build the executor's graph, choosing K by timing when not forced.  The
+// caller holds g_exec_mu.
 sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
     const int n = (int)e->plans.size();
+    // The same plans with other buffers (double-buffered input and output):
+    // the branch count and chunking depend on the boxes only, so take the
+    // existing executor's choice instead of timing the candidates again.
+    for (const BatchExec* c : g_execs) {
+        if (c == e || !c->exec || c->plans != e->plans) continue;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        const sbp_status s = capture_batch(e, c->branches, c->chunked != 0, &g, &x);
+        if (s != SBP_OK) return s;
+        e->graph = g;
+        e->exec = x;
+        e->branches = c->branches;
+        e->chunked = c->chunked;
+        e->tuned_ms = c->tuned_ms;
+        return SBP_OK;
+    }
     std::vector<int> cands;
     if (const char* env = std::getenv("SBP_BATCH_BRANCHES")) {
         const int k = std::atoi(env);

@@ -146,6 +146,30 @@ def test_batched_uneven_boxes_repeated_calls(sbp, dtype):
     assert rel_l2(outs[3].double().cpu().numpy(), want) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batched_double_buffered(sbp, dtype):
+    # two buffer sets for the same plans: the second executor takes the first
+    # one's branch count and chunking, and both give the single solves' bits
+    import torch
+
+    shapes = [(128, 128, 64), (64, 64, 32), (96, 48, 24)]
+    rng = np.random.default_rng(21)
+    boxes = [W.Box(nx, ny, nz, 2.0, 3.0, 1.5) for nx, ny, nz in shapes]
+    plans = [_plan(sbp, b, dtype) for b in boxes]
+    sets = []
+    for _ in range(2):
+        rhos = [to_dev(rng.standard_normal((b.nz, b.ny, b.nx)), dtype) for b in boxes]
+        sets.append((rhos, [torch.empty_like(r) for r in rhos]))
+    ts = [0.3, 1.7, -0.9]
+    for _ in range(2):
+        for rhos, outs in sets:
+            sbp.solve_batched(plans, rhos, outs, ts)
+    torch.cuda.synchronize()
+    for rhos, outs in sets:
+        for i, p in enumerate(plans):
+            assert torch.equal(outs[i], p.solve(rhos[i], t=ts[i])), i
+
+
 def test_partial_overlap_rejected(sbp):
     import torch
 
