@@ -429,13 +429,17 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forw
     if constexpr (sizeof(T) == 4) {
         if (tile_sums != nullptr) {
             // FP64-quality plane sums from error-free float additions
-            FF acc = {0.f, 0.f};
+            // two compensated accumulators (even and odd row of the pair) as
+            // one packed pair: y = x + lo, t = hi + y, lo = y - (t - hi), hi = t
+            cpx<float> hi = {0.f, 0.f}, lo = {0.f, 0.f};
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                kahan_add(acc, (float)v[0][e].x);
-                kahan_add(acc, (float)v[0][e].y);
+                const cpx<float> y = cadd(cpx<float>{(float)v[0][e].x, (float)v[0][e].y}, lo);
+                const cpx<float> tt = cadd(hi, y);
+                lo = csub(y, csub(tt, hi));
+                hi = tt;
             }
-            const FF tot = block_sum_ff(acc);
+            const FF tot = block_sum_ff(ff_add(FF{hi.x, lo.x}, FF{hi.y, lo.y}));
             if (tid == 0) tile_sums[bid] = (double)tot.hi + (double)tot.lo;
         }
     } else {
@@ -1065,11 +1069,16 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_inve
         T p0 = v[0][e].x, p1 = -v[0][e].y;  // conj of the forward result
         if (addk0) {
             if constexpr (sizeof(T) == 4) {
-                float s, er;
-                two_sum(p0, add_hi, s, er);
-                p0 = s + (er + add_lo);
-                two_sum(p1, add_hi, s, er);
-                p1 = s + (er + add_lo);
+                // TwoSum of (p0, p1) + hi, then + lo, on both rows at once as
+                // packed pairs: the same operations and roundings as the
+                // scalar form, in half the instructions
+                const cpx<float> a = {p0, p1}, hh = {add_hi, add_hi}, ll = {add_lo, add_lo};
+                const cpx<float> sm = cadd(a, hh);
+                const cpx<float> bb = csub(sm, a);
+                const cpx<float> er = cadd(csub(a, csub(sm, bb)), csub(hh, bb));
+                const cpx<float> r = cadd(sm, cadd(er, ll));
+                p0 = r.x;
+                p1 = r.y;
             } else {
                 p0 = p0 + add_hi;
                 p1 = p1 + add_hi;

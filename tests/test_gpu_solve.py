@@ -219,6 +219,36 @@ def test_box256_sampled(sbp, dtype):
 
 
 @pytest.mark.slow
+def test_batch96_as_benchmarked(sbp):
+    # The 96-box FP32 batch exactly as bench.py times it (same boxes, densities,
+    # shear times and sbp_solve_batched with its tuned branch count and
+    # chunking): every box bit-identical to its own single solve, and one box
+    # of each size against the oracle's one-by-one sampled outputs.
+    import torch
+
+    case = W.batch_96()
+    boxes, times = case.boxes, [float(t) for t in case.times]
+    rhos_np = [W.lognormal_disc(b, seed=s, sigma=0.7, dtype=np.float32) for b, s in zip(boxes, case.seeds)]
+    plans = [_plan(sbp, b, 1) for b in boxes]
+    rhos = [to_dev(r, 1) for r in rhos_np]
+    outs = [torch.empty_like(r) for r in rhos]
+    for _ in range(2):  # the first call tunes and captures, the second replays
+        sbp.solve_batched(plans, rhos, outs, times)
+    torch.cuda.synchronize()
+    for i, p in enumerate(plans):
+        assert torch.equal(outs[i], p.solve(rhos[i], t=times[i])), i
+    rng = np.random.default_rng(96)
+    for i in (0, 33, 66, 95):  # 64³, 128²×64, 192²×96, 256²×128
+        b = boxes[i]
+        pts = [(0, 0, 0), (b.nz - 1, b.ny - 1, b.nx - 1)]
+        pts += [(int(rng.integers(b.nz)), int(rng.integers(b.ny)), int(rng.integers(b.nx))) for _ in range(6)]
+        got_full = outs[i].double().cpu().numpy()
+        got = np.array([got_full[k, y, x] for (k, y, x) in pts])
+        want = O.solve_at(as_input(rhos_np[i], 1), _params(b), times[i], pts)
+        assert rel_l2(got, want) <= TOL[1], i
+
+
+@pytest.mark.slow
 def test_box256_properties(sbp):
     import torch
 
