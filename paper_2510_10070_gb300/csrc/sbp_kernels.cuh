@@ -398,7 +398,8 @@ __device__ __forceinline__ void store_rows_from_smem(T* __restrict__ dst, const 
 // x forward: C row pairs per block (2C consecutive real rows of one plane).
 // Lanes run along x (t fastest), so each thread loads its E elements of both
 // rows straight from global memory with coalesced loads.
-// smem: tw[n] | C padded rows (exchange, then the paired spectrum Z)
+// smem: tw[n] | C padded rows (the FFT's exchange; for runtime lengths and
+// row pairs wider than a warp, also the paired spectrum Z for the split)
 // ---------------------------------------------------------------------------
 template <typename T, int E, int NS>
 __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
