@@ -14,11 +14,15 @@
 //            accumulated in FP32 (mma.sync m16n8k16), 12 MMAs per 8 transforms,
 //            the data moved between shared memory and fragments each repetition
 //            (as it would have to be inside a pass);
-//   mma1     the hi·hi product alone (the error before the split recovery).
+//   mma1     the hi·hi product alone (the error before the split recovery);
+//   mma3_bf16, mma1_bf16   the same two with the operands split in BF16
+//            (mma.sync m16n8k16 .bf16.bf16: 8 mantissa bits instead of 11,
+//            FP32's exponent range).
 //
 // Build and run through `python -m paper_2510_10070_gb300.a10.run`; prints one
 // JSON line.  Not part of the library: it only measures whether the option
 // pays.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -36,30 +40,50 @@ constexpr int kThreads = 256;     // one transform per thread (cc), 32 per warp 
 constexpr int kTile = kThreads;   // transforms per block
 constexpr int kStride = kTile + 4;  // padded row of the [16][tile] planes (conflict-free fragments)
 
-__device__ __forceinline__ uint32_t pack_h2(float lo_col, float hi_col) {
-    __half2 h = __floats2half2_rn(lo_col, hi_col);
-    return *reinterpret_cast<uint32_t*>(&h);
-}
-// x = hi + lo with hi = fp16(x), lo = fp16(x - hi)
+// x = hi + lo with hi = h(x), lo = h(x - hi), h = FP16 or BF16 rounding;
+// two values packed per 32-bit fragment register (first in the low half)
+template <bool BF>
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-    const float ra = a - __half2float(ha), rb = b - __half2float(hb);
-    __half2 h = __halves2half2(ha, hb);
-    hi = *reinterpret_cast<uint32_t*>(&h);
-    lo = pack_h2(ra, rb);
+    if constexpr (BF) {
+        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+        const float ra = a - __bfloat162float(ha), rb = b - __bfloat162float(hb);
+        __nv_bfloat162 h = __halves2bfloat162(ha, hb);
+        __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    } else {
+        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+        const float ra = a - __half2float(ha), rb = b - __half2float(hb);
+        __half2 h = __halves2half2(ha, hb);
+        __half2 l = __floats2half2_rn(ra, rb);
+        hi = *reinterpret_cast<uint32_t*>(&h);
+        lo = *reinterpret_cast<uint32_t*>(&l);
+    }
 }
 
+// D += A·B, A and B of the same 16-bit type (FP16 or BF16), FP32 accumulate
+template <bool BF>
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    if constexpr (BF) {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    } else {
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+            "{%0,%1,%2,%3};"
+            : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    }
 }
 
 // In-place DFTs of the block's tile, reps times; data as planes re[16][kStride], im[16][kStride].
-template <int MODE>  // 0: cc_reg, 1: cc_smem, 2: mma3, 3: mma1
+template <int MODE>  // 0: cc_reg, 1: cc_smem, 2: mma3, 3: mma1, 4: mma3_bf16, 5: mma1_bf16
 __global__ void __launch_bounds__(kThreads) k_dft16(float* __restrict__ data, int reps) {
+    constexpr bool BF = (MODE >= 4);
+    constexpr bool THREE = (MODE == 2 || MODE == 4);
     __shared__ float re[16 * kStride], im[16 * kStride];
     const int tid = threadIdx.x;
     float* blk = data + (size_t)blockIdx.x * kTile * 32;  // [tile][16] complex, interleaved
@@ -103,9 +127,9 @@ __global__ void __launch_bounds__(kThreads) k_dft16(float* __restrict__ data, in
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int m = rows[q], k = cols[q];
-                split2(fre(m, k), fre(m, k + 1), fr_h[q], fr_l[q]);
-                split2(fim(m, k), fim(m, k + 1), fi_h[q], fi_l[q]);
-                split2(-fim(m, k), -fim(m, k + 1), fn_h[q], fn_l[q]);
+                split2<BF>(fre(m, k), fre(m, k + 1), fr_h[q], fr_l[q]);
+                split2<BF>(fim(m, k), fim(m, k + 1), fi_h[q], fi_l[q]);
+                split2<BF>(-fim(m, k), -fim(m, k + 1), fn_h[q], fn_l[q]);
             }
         }
         for (int r = 0; r < reps; ++r) {
@@ -113,25 +137,25 @@ __global__ void __launch_bounds__(kThreads) k_dft16(float* __restrict__ data, in
             for (int grp = 0; grp < 4; ++grp) {  // 8 transforms per group, 4 groups per warp
                 const int col = warp * 32 + grp * 8;
                 uint32_t xr_h0, xr_l0, xr_h1, xr_l1, xi_h0, xi_l0, xi_h1, xi_l1;
-                split2(re[(2 * t) * kStride + col + g], re[(2 * t + 1) * kStride + col + g], xr_h0, xr_l0);
-                split2(re[(2 * t + 8) * kStride + col + g], re[(2 * t + 9) * kStride + col + g], xr_h1, xr_l1);
-                split2(im[(2 * t) * kStride + col + g], im[(2 * t + 1) * kStride + col + g], xi_h0, xi_l0);
-                split2(im[(2 * t + 8) * kStride + col + g], im[(2 * t + 9) * kStride + col + g], xi_h1, xi_l1);
+                split2<BF>(re[(2 * t) * kStride + col + g], re[(2 * t + 1) * kStride + col + g], xr_h0, xr_l0);
+                split2<BF>(re[(2 * t + 8) * kStride + col + g], re[(2 * t + 9) * kStride + col + g], xr_h1, xr_l1);
+                split2<BF>(im[(2 * t) * kStride + col + g], im[(2 * t + 1) * kStride + col + g], xi_h0, xi_l0);
+                split2<BF>(im[(2 * t + 8) * kStride + col + g], im[(2 * t + 9) * kStride + col + g], xi_h1, xi_l1);
                 float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
                 // Re y = Re F·Re x - Im F·Im x;  Im y = Im F·Re x + Re F·Im x
-                mma16816(yr, fr_h, xr_h0, xr_h1);
-                mma16816(yr, fn_h, xi_h0, xi_h1);
-                mma16816(yi, fi_h, xr_h0, xr_h1);
-                mma16816(yi, fr_h, xi_h0, xi_h1);
-                if constexpr (MODE == 2) {
-                    mma16816(yr, fr_h, xr_l0, xr_l1);
-                    mma16816(yr, fr_l, xr_h0, xr_h1);
-                    mma16816(yr, fn_h, xi_l0, xi_l1);
-                    mma16816(yr, fn_l, xi_h0, xi_h1);
-                    mma16816(yi, fi_h, xr_l0, xr_l1);
-                    mma16816(yi, fi_l, xr_h0, xr_h1);
-                    mma16816(yi, fr_h, xi_l0, xi_l1);
-                    mma16816(yi, fr_l, xi_h0, xi_h1);
+                mma16816<BF>(yr, fr_h, xr_h0, xr_h1);
+                mma16816<BF>(yr, fn_h, xi_h0, xi_h1);
+                mma16816<BF>(yi, fi_h, xr_h0, xr_h1);
+                mma16816<BF>(yi, fr_h, xi_h0, xi_h1);
+                if constexpr (THREE) {
+                    mma16816<BF>(yr, fr_h, xr_l0, xr_l1);
+                    mma16816<BF>(yr, fr_l, xr_h0, xr_h1);
+                    mma16816<BF>(yr, fn_h, xi_l0, xi_l1);
+                    mma16816<BF>(yr, fn_l, xi_h0, xi_h1);
+                    mma16816<BF>(yi, fi_h, xr_l0, xr_l1);
+                    mma16816<BF>(yi, fi_l, xr_h0, xr_h1);
+                    mma16816<BF>(yi, fr_h, xi_l0, xi_l1);
+                    mma16816<BF>(yi, fr_l, xi_h0, xi_h1);
                 }
                 __syncwarp();
                 re[g * kStride + col + 2 * t] = yr[0];
@@ -189,16 +213,18 @@ int main(int argc, char** argv) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    const char* names[4] = {"cc_reg", "cc_smem", "mma3", "mma1"};
+    const char* names[6] = {"cc_reg", "cc_smem", "mma3", "mma1", "mma3_bf16", "mma1_bf16"};
     std::printf("{\"transforms\": %d, \"reps\": %d", ndft, reps);
-    for (int mode = 0; mode < 4; ++mode) {
+    for (int mode = 0; mode < 6; ++mode) {
         // accuracy: one repetition
         cudaMemcpy(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
         switch (mode) {
             case 0: k_dft16<0><<<blocks, kThreads>>>(d, 1); break;
             case 1: k_dft16<1><<<blocks, kThreads>>>(d, 1); break;
             case 2: k_dft16<2><<<blocks, kThreads>>>(d, 1); break;
-            default: k_dft16<3><<<blocks, kThreads>>>(d, 1); break;
+            case 3: k_dft16<3><<<blocks, kThreads>>>(d, 1); break;
+            case 4: k_dft16<4><<<blocks, kThreads>>>(d, 1); break;
+            default: k_dft16<5><<<blocks, kThreads>>>(d, 1); break;
         }
         std::vector<float> out(h.size());
         if (cudaMemcpy(out.data(), d, out.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) return 2;
@@ -212,7 +238,9 @@ int main(int argc, char** argv) {
                 case 0: k_dft16<0><<<blocks, kThreads>>>(d, reps); break;
                 case 1: k_dft16<1><<<blocks, kThreads>>>(d, reps); break;
                 case 2: k_dft16<2><<<blocks, kThreads>>>(d, reps); break;
-                default: k_dft16<3><<<blocks, kThreads>>>(d, reps); break;
+                case 3: k_dft16<3><<<blocks, kThreads>>>(d, reps); break;
+                case 4: k_dft16<4><<<blocks, kThreads>>>(d, reps); break;
+                default: k_dft16<5><<<blocks, kThreads>>>(d, reps); break;
             }
             cudaEventRecord(b);
             cudaEventSynchronize(b);

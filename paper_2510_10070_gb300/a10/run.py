@@ -1,5 +1,5 @@
 """Build and run the radix-16 measurement: 16-point DFTs on the CUDA cores
-(the FFT engine's butterfly) and on the tensor cores (FP16 hi/lo split,
+(the FFT engine's butterfly) and on the tensor cores (FP16 and BF16 hi/lo splits,
 mma.sync), with their errors against an FP64 DFT.
 
     python -m paper_2510_10070_gb300.a10.run [--blocks 1216] [--reps 64]
