@@ -226,6 +226,8 @@ class Plan:
 def solve_batched(plans, rhos, phis, ts, stream=None):
     """Solve box i with plans[i] at time ts[i] (one call, one stream)."""
     n = len(plans)
+    if not (len(rhos) == len(phis) == len(ts) == n):
+        raise ValueError("plans, rhos, phis and ts must have the same length")
     for p, r, f in zip(plans, rhos, phis):
         p._check_tensor(r, "rho")
         p._check_tensor(f, "phi")

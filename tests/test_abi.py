@@ -85,3 +85,11 @@ def test_invalid_dtype_and_null_args(lib):
     lib.sbp_plan_destroy(None)  # NULL-safe
     assert lib.sbp_solve_batched(-1, None, None, None, None, None) == 1
     assert lib.sbp_solve_batched(0, None, None, None, None, None) == 0
+
+
+def test_binding_checks_batch_lengths():
+    # argument marshalling only: mismatched list lengths never reach the library
+    from paper_2510_10070_gb300 import sbp
+
+    with pytest.raises(ValueError):
+        sbp.solve_batched([], [], [], [1.0])

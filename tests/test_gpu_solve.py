@@ -170,6 +170,17 @@ def test_batched_double_buffered(sbp, dtype):
             assert torch.equal(outs[i], p.solve(rhos[i], t=ts[i])), i
 
 
+def test_empty_batch_and_length_mismatch(sbp):
+    import torch
+
+    sbp.solve_batched([], [], [], [])  # nothing to do: SBP_OK
+    box = W.Box(16, 16, 8, 1.0, 1.0, 1.0)
+    plan = _plan(sbp, box, 1)
+    r = torch.zeros((8, 16, 16), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        sbp.solve_batched([plan], [r], [torch.empty_like(r)], [0.1, 0.2])
+
+
 def test_partial_overlap_rejected(sbp):
     import torch
 
