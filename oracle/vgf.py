@@ -26,7 +26,7 @@ Written as direct sums (no FFT anywhere):
     Φ̂(a, b, i)  = Σ_{j<N_z} c_{i-j}(a, b) R(a, b, j)
     Φ̃[i, y, x]  = 4πG / (N_x N_y) · Re Σ_{a,b} Φ̂(a, b, i) exp(+2πi (...))
 
-Readings of the paper that this module takes (each one listed in the design doc):
+Readings of the paper that this module takes (where the paper is silent or garbled):
 
 * padding M = 2 N_z with L = L_z (α = 1); the paper's α = 1.1 needs M = 4 N_z
   and is available through ``SolveParams(pad=4, alpha=1.1)``;
