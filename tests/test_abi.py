@@ -93,3 +93,30 @@ def test_binding_checks_batch_lengths():
 
     with pytest.raises(ValueError):
         sbp.solve_batched([], [], [], [1.0])
+
+
+def _header_enum(prefix):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(" + prefix + r"[A-Z0-9_]*)\s*=\s*(\d+)", text)}
+
+
+@pytest.mark.parametrize("enum_name,prefix,strip", [
+    ("DType", "SBP_F", "SBP_"),
+    ("Stage", "SBP_STAGE_", "SBP_STAGE_"),
+    ("Option", "SBP_OPT_", "SBP_OPT_"),
+])
+def test_binding_enums_match_the_header(enum_name, prefix, strip):
+    # the binding's enums carry exactly the header's names and values
+    from paper_2510_10070_gb300 import sbp
+
+    want = {k[len(strip):]: v for k, v in _header_enum(prefix).items()}
+    got = {m.name: int(m.value) for m in getattr(sbp, enum_name)}
+    assert got == want
+
+
+def test_binding_status_codes_match_the_header():
+    from paper_2510_10070_gb300 import sbp
+
+    want = {k.replace("SBP_ERR_", "").replace("SBP_", ""): v for k, v in _header_enum("SBP_(?:ERR_|OK)").items()}
+    got = {m.name: int(m.value) for m in sbp.Status}
+    assert got == want
