@@ -26,6 +26,12 @@ constexpr int kMaxThreads = 256;  // threads per block of every pass kernel
 // z pass 3; FP64 and 24-element variants keep 2 so that they do not spill.
 template <typename T, int E>
 constexpr int min_blocks_xy() { return (sizeof(T) == 8 || E > 16) ? 2 : 4; }
+// The static-length FP32 x passes and TMA y passes up to 256 fit in 48
+// registers without spills, which makes room for a fifth block (40 warps) per
+// SM: their time goes to waiting on memory and barriers, so more resident
+// warps overlap more of it.
+template <typename T, int E, int NS>
+constexpr int min_blocks_xs() { return (sizeof(T) == 4 && E == 16 && NS > 0 && NS <= 256) ? 5 : min_blocks_xy<T, E>(); }
 template <typename T, int E>
 constexpr int min_blocks_z() { return (sizeof(T) == 8 || E > 16) ? 2 : 3; }
 // The padded z kernel fits 64 registers at E = 16 (its radix-16 stages apply
@@ -402,7 +408,7 @@ __device__ __forceinline__ void store_rows_from_smem(T* __restrict__ dst, const 
 // row pairs wider than a warp, also the paired spectrum Z for the split)
 // ---------------------------------------------------------------------------
 template <typename T, int E, int NS>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xs<T, E, NS>())) k_x_forward(const T* __restrict__ rho, cpx<T>* __restrict__ W,
                                                            const cpx<T>* __restrict__ twg,
                                                            double* __restrict__ tile_sums, XArgs A) {
     if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
@@ -564,7 +570,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_y_pass
 // results are stored straight from registers.
 // smem: tile [NS][CS] (128-byte aligned; later the exchange, TileCol) | tw[NS] | mbarrier
 template <typename T, int E, bool INV, int NS, int CS>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xs<T, E, NS>()))
     k_y_tma(cpx<T>* __restrict__ W, const cpx<T>* __restrict__ twg, YArgs A, TmaCtl ctl,
             const __grid_constant__ CUtensorMap tmap) {
     constexpr int Tf = NS / E;
@@ -1017,7 +1023,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_z<T, E>())) k_z_paper
 // smem: tw[n] | C padded rows (exchange)
 // ---------------------------------------------------------------------------
 template <typename T, int E, int NS>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>())) k_x_inverse(const cpx<T>* __restrict__ W, T* __restrict__ phi,
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xs<T, E, NS>())) k_x_inverse(const cpx<T>* __restrict__ W, T* __restrict__ phi,
                                                            const cpx<T>* __restrict__ twg, XArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = NS > 0 ? NS : A.P.n, C = A.C, Tf = NS > 0 ? NS / E : A.P.Tf;
