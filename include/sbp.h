@@ -114,9 +114,12 @@ sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* str
  * Execution: the boxes' pass kernels are captured once into a CUDA graph with
  * K parallel branches and cached by the exact (plans, rho, phi) tuple; a call
  * with a cached tuple copies the nbox shear parameters to the device and
- * replays the graph on `stream`.  The first call of a tuple chooses K by
- * timing candidate graphs on `stream` (it synchronises that stream once);
- * the environment variable SBP_BATCH_BRANCHES=K forces K.  Destroying any
+ * replays the graph on `stream`.  The first call of a tuple chooses K (and
+ * whether the x/y passes run in L2-sized chunks) by timing candidate graphs
+ * on `stream` (it synchronises that stream once); a later tuple with the same
+ * plans and other buffers (double buffering) takes that choice without
+ * timing.  The environment variables SBP_BATCH_BRANCHES=K and
+ * SBP_BATCH_CHUNK=0/1 force the choice.  Destroying or reconfiguring any
  * plan of a tuple drops its cached graph.
  */
 sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const* rho,
