@@ -91,7 +91,7 @@ __device__ __forceinline__ double column_turns(double sig, int x, int nx) {
 // A_k = (Z_k + conj Z_{N-k})/2, B_k = -i (Z_k - conj Z_{N-k})/2.
 // smem: tw[NY] | exchange (XchgCol)
 template <typename T, int E, int NY, int CP>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
+__global__ void __launch_bounds__(kMaxThreads, (NY >= 64 ? min_blocks_xs<T, E, NY>() : min_blocks_xy<T, E>()))
     k_ry_forward(const T* __restrict__ rho, cpx<T>* __restrict__ V, const cpx<T>* __restrict__ twg,
                  double* __restrict__ tile_sums, RArgs A) {
     if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
 // or unnormalised inverse.  Block = C rows; lanes along the row.
 // smem: tw[NX] | C padded rows
 template <typename T, int E, int NX, bool INV>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
+__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xs<T, E, NX>()))
     k_rows_c2c(cpx<T>* __restrict__ V, const cpx<T>* __restrict__ twg, int rows, int pitch) {
     constexpr int Tf = NX / E;
     constexpr int C = kMaxThreads / Tf;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
 // transform per pair, φ(x_a) = Re, φ(x_b) = Im; the FP32 path adds the FP64
 // mean mode of the plane.  smem: tw[NY] | exchange (XchgCol)
 template <typename T, int E, int NY, int CP>
-__global__ void __launch_bounds__(kMaxThreads, (min_blocks_xy<T, E>()))
+__global__ void __launch_bounds__(kMaxThreads, (NY >= 64 ? min_blocks_xs<T, E, NY>() : min_blocks_xy<T, E>()))
     k_ry_inverse(const cpx<T>* __restrict__ V, T* __restrict__ phi, const cpx<T>* __restrict__ twg, RArgs A) {
     const int bid = blockIdx.x;
     const int z = bid / A.tiles, tile = bid - z * A.tiles;
