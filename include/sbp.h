@@ -110,13 +110,18 @@ sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* str
  * (bit for bit).  All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE)
  * and the device.  A plan may appear only once per call.  plans, rho, phi and
  * t are HOST arrays of length nbox; rho[i] and phi[i] are device pointers.
+ * phi[i] == rho[i] (in place) is allowed, as in sbp_solve.  The boxes run
+ * concurrently, so a box's phi must not overlap another box's rho or phi
+ * (SBP_ERR_INVALID_ARG); boxes may share the same rho.
  *
  * Execution: the boxes' pass kernels are captured once into a CUDA graph with
  * K parallel branches and cached by the exact (plans, rho, phi) tuple; a call
  * with a cached tuple copies the nbox shear parameters to the device and
  * replays the graph on `stream`.  The first call of a tuple chooses K (and
  * whether the x/y passes run in L2-sized chunks) by timing candidate graphs
- * on `stream` (it synchronises that stream once); a later tuple with the same
+ * on `stream` (it synchronises that stream once); the candidates write into
+ * temporary outputs that the call allocates and frees, so the caller's
+ * buffers see exactly one solve per call; a later tuple with the same
  * plans and other buffers (double buffering) takes that choice without
  * timing.  The environment variables SBP_BATCH_BRANCHES=K and
  * SBP_BATCH_CHUNK=0/1 force the choice.  Destroying or reconfiguring any
@@ -154,7 +159,12 @@ enum {
     SBP_OPT_Y_TMA = 3,
     /* Clock cycles a kernel may wait for an asynchronous copy before it gives
      * up, records the timeout in the plan's status word and returns
-     * (default 2e9, about one second). */
+     * (default 2e9, about one second).  A block whose copy was issued but is
+     * late waits once more, for the same budget, before it returns, so that
+     * the copy cannot land in shared memory given to another block.  After
+     * SBP_ERR_DEVICE_TIMEOUT the outputs of that solve are undefined; if the
+     * copy was still missing after the second wait, so are the outputs of
+     * kernels that ran beside it, and the context is best torn down. */
     SBP_OPT_SPIN_BUDGET = 4,
     /* Test switch: 1 makes the TMA kernels arm no copy, so that their bounded
      * waits run out (the results are then undefined and
@@ -279,7 +289,11 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  *                         half-spectrum inverse x DFT (real part, unscaled).
  *   SBP_STAGE_GREEN_TABLE: in ignored, out = double [ny][nx/2+1][4] holding
  *                         (k², 1 - e^{-kL}, k_p², 1 - e^{-k_p L}) for each
- *                         stored mode and its Hermitian partner at time t.
+ *                         stored mode and its Hermitian partner at time t:
+ *                         the plan's internal table as a solve reads it,
+ *                         computed in FP64 and stored in the plan's real type
+ *                         (an SBP_F32 plan holds the FP64 values rounded once
+ *                         to float), widened to double.
  * The FP32 mean-mode side path is not part of any single stage.
  */
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream);
@@ -303,9 +317,11 @@ sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, doubl
  * 256×256×128 cells is the largest cube-like box that does) returns
  * SBP_ERR_SCRATCH_LIMIT before touching the device.
  *
- * The first call on each device looks up the array's device address (with
- * that device current) and caches it; make that first call before any CUDA
- * stream capture.  Every call on a device shares the array, which keeps the
+ * Its tables (twiddles, k_z², the FP64 k = 0 kernel) are built by a kernel
+ * inside the array on every call; no host memory is copied.  The first call
+ * on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any CUDA stream
+ * capture.  Every call on a device shares the array, which keeps the
  * last call's contents (every byte a call reads is written earlier in the
  * same call, so nothing needs clearing).  Calls whose work overlaps on the
  * GPU, for example on two streams, race on the array: order them.

@@ -19,23 +19,6 @@
 
 using namespace sbp;
 
-namespace sbp {
-// ---------------------------------------------------------------------------
-// Green's parameter table (stage-level testing): out[b][a][4].
-// ---------------------------------------------------------------------------
-__global__ void k_green_table(double* __restrict__ out, int nx, int ny, double Lx, double Ly, double L, double s) {
-    const int h = nx / 2 + 1;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= h * ny) return;
-    const int b = q / h, a = q - b * h;
-    const GreenMode g = green_mode(a, b, nx, ny, Lx, Ly, L, s);
-    out[4 * q + 0] = g.k2a;
-    out[4 * q + 1] = g.omEa;
-    out[4 * q + 2] = g.k2b;
-    out[4 * q + 3] = g.omEb;
-}
-
-}  // namespace sbp
 
 namespace {
 
@@ -849,9 +832,12 @@ sbp_status launch_stage(sbp_plan_s* p, int stage, const void* in, void* out, dou
             break;
         }
         case SBP_STAGE_GREEN_TABLE: {
+            // fill the plan's table exactly as a solve does, then report it as stored
             const int total = p->h * p->ny;
-            k_green_table<<<(total + 255) / 256, 256, 0, st>>>(static_cast<double*>(out), p->nx, p->ny, p->Lx,
-                                                             p->Ly, p->Lz, shear_s(p, t));
+            const int blocks = (total + 255) / 256;
+            k_green_params<T><<<blocks, 256, 0, st>>>(make_green_fill(p, t, blocks));
+            k_green_dump<T><<<blocks, 256, 0, st>>>(static_cast<const GreenT<T>*>(p->green),
+                                                   static_cast<double*>(out), total);
             break;
         }
         default:
@@ -1216,6 +1202,7 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
         cudaGetLastError();
+        if (a) cudaEventDestroy(a);
         return SBP_ERR_CUDA;
     }
     // chunked x/y passes only where some box has more than one chunk
@@ -1232,6 +1219,39 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
     std::vector<std::pair<int, int>> trials;
     for (int K : cands)
         for (int c : chunk_modes) trials.push_back({K, c});
+    // The candidate graphs are replayed several times to time them.  They
+    // write into temporary outputs, never into the caller's phi: an in-place
+    // box (phi == rho) would otherwise be solved again on every replay, and
+    // the caller's rho stays untouched.  The chosen configuration is captured
+    // once more on the caller's buffers below and replayed once by the caller.
+    std::vector<void*> caller_phi = e->phi;
+    void* scratch = nullptr;
+    if (trials.size() > 1) {
+        std::vector<size_t> offs(n);
+        size_t total = 0;
+        for (int i = 0; i < n; ++i) {
+            const sbp_plan_s* p = e->plans[i];
+            offs[i] = total;
+            total = align_up(total + (size_t)p->nx * p->ny * p->nz * p->rsize, 256);
+        }
+        if (cudaMalloc(&scratch, std::max<size_t>(total, 256)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return SBP_ERR_OUT_OF_MEMORY;
+        }
+        for (int i = 0; i < n; ++i) e->phi[i] = static_cast<unsigned char*>(scratch) + offs[i];
+    }
+    auto restore = [&]() {
+        e->phi = caller_phi;
+        if (scratch) {
+            cudaStreamSynchronize(st);
+            cudaFree(scratch);
+            scratch = nullptr;
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    };
     float best = 0.f;
     for (const auto& tr : trials) {
         const int K = tr.first;
@@ -1239,8 +1259,7 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
         cudaGraphExec_t x = nullptr;
         const sbp_status s = capture_batch(e, K, tr.second != 0, &g, &x);
         if (s != SBP_OK) {
-            if (a) cudaEventDestroy(a);
-            if (b) cudaEventDestroy(b);
+            restore();
             return s;
         }
         float ms = 0.f;
@@ -1252,9 +1271,8 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
             if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
                 cudaGraphExecDestroy(x);
                 cudaGraphDestroy(g);
-                cudaEventDestroy(a);
-                cudaEventDestroy(b);
                 cudaGetLastError();
+                restore();
                 return SBP_ERR_CUDA;
             }
         }
@@ -1272,8 +1290,21 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
         }
     }
     e->tuned_ms = best / 3.f;
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
+    const bool timed = (scratch != nullptr);
+    restore();
+    if (timed) {
+        // the kept graph wrote into the temporaries: capture it again on the caller's buffers
+        cudaGraphExecDestroy(e->exec);
+        cudaGraphDestroy(e->graph);
+        e->exec = nullptr;
+        e->graph = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        const sbp_status s = capture_batch(e, e->branches, e->chunked != 0, &g, &x);
+        if (s != SBP_OK) return s;
+        e->graph = g;
+        e->exec = x;
+    }
     return SBP_OK;
 }
 
@@ -1425,6 +1456,27 @@ sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const*
             if (plans[j] == plans[i]) return SBP_ERR_INVALID_ARG;
         const sbp_status v = check_io(plans[i], rho[i], phi[i], t[i]);
         if (v != SBP_OK) return v;
+    }
+    // Boxes run concurrently: no box may write memory that another box reads
+    // or writes (two boxes reading the same rho is fine).
+    {
+        struct Span {
+            uintptr_t lo, hi;
+            int box;
+            bool write;
+        };
+        std::vector<Span> spans;
+        spans.reserve(2 * (size_t)nbox);
+        for (int i = 0; i < nbox; ++i) {
+            const size_t bytes = (size_t)plans[i]->nx * plans[i]->ny * plans[i]->nz * plans[i]->rsize;
+            const uintptr_t r0 = reinterpret_cast<uintptr_t>(rho[i]), f0 = reinterpret_cast<uintptr_t>(phi[i]);
+            spans.push_back({r0, r0 + bytes, i, false});
+            spans.push_back({f0, f0 + bytes, i, true});
+        }
+        std::sort(spans.begin(), spans.end(), [](const Span& x, const Span& y) { return x.lo < y.lo; });
+        for (size_t u = 0; u < spans.size(); ++u)
+            for (size_t w = u + 1; w < spans.size() && spans[w].lo < spans[u].hi; ++w)
+                if (spans[u].box != spans[w].box && (spans[u].write || spans[w].write)) return SBP_ERR_INVALID_ARG;
     }
     if (nbox == 0) return SBP_OK;
     DeviceGuard g(plans[0]->device);

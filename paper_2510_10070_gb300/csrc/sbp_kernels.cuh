@@ -287,40 +287,6 @@ __device__ __forceinline__ GreenMode green_mode(int a, int b, int nx, int ny, do
     return g;
 }
 
-// The same parameters in FP32 for the FP32 path: |k|² and expm1 to float
-// rounding (relative error about 1e-7, far inside the FP32 tolerance), at the
-// FP32 rate instead of GB300's 1/64-rate FP64 pipe.
-struct GreenModeF {
-    float k2a, omEa, k2b, omEb;
-    int kzero, same;
-};
-__device__ __forceinline__ GreenModeF green_mode_f(int a, int b, int nx, int ny, float kxs, float kys, float L,
-                                                   float s) {
-    GreenModeF g;
-    const int as = (a < nx / 2) ? a : a - nx;
-    const int bs = (b < ny / 2) ? b : b - ny;
-    const int ap = wrap_signed(-as, nx);
-    const int bp = wrap_signed(-bs, ny);
-    g.kzero = (as == 0 && bs == 0);
-    {
-        const float Kx = kxs * (float)as, Ky = kys * (float)bs;
-        const float kx = fmaf(s, Ky, Kx);
-        g.k2a = fmaf(kx, kx, Ky * Ky);
-        g.omEa = g.kzero ? 0.f : -expm1f(-sqrtf(g.k2a) * L);
-    }
-    g.same = (ap == -as && bp == -bs);
-    if (g.same) {
-        g.k2b = g.k2a;
-        g.omEb = g.omEa;
-    } else {
-        const float Kx = kxs * (float)ap, Ky = kys * (float)bp;
-        const float kx = fmaf(s, Ky, Kx);
-        g.k2b = fmaf(kx, kx, Ky * Ky);
-        g.omEb = -expm1f(-sqrtf(g.k2b) * L);
-    }
-    return g;
-}
-
 template <typename T>
 __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     if (gf.tab == nullptr) return;
@@ -330,21 +296,27 @@ __device__ __forceinline__ void green_fill(const GreenFill& gf, int block) {
     const int q0 = block * gf.per_block;
     const int q1 = min(total, q0 + gf.per_block);
     const double s = gf.s_dev != nullptr ? *gf.s_dev : gf.s;
-    if constexpr (sizeof(T) == 4) {
-        const float kxs = (float)(kTwoPi / gf.Lx), kys = (float)(kTwoPi / gf.Ly);
-        const float L = (float)gf.L, sf = (float)s;
-        for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
-            const int b = q / h, a = q - b * h;
-            const GreenModeF g = green_mode_f(a, b, gf.nx, gf.ny, kxs, kys, L, sf);
-            tab[q] = GreenT<T>{g.k2a, g.omEa, g.k2b, g.omEb, g.kzero, g.same};
-        }
-    } else {
-        for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
-            const int b = q / h, a = q - b * h;
-            const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, s);
-            tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
-        }
+    // FP64 for every plan type (the FP32 path stores the FP64 values rounded
+    // once to float): one table entry per thread, spread over the blocks the
+    // caller reserves for it, so the 1/64-rate FP64 pipe of many SMs shares it.
+    for (int q = q0 + (int)threadIdx.x; q < q1; q += blockDim.x) {
+        const int b = q / h, a = q - b * h;
+        const GreenMode g = green_mode(a, b, gf.nx, gf.ny, gf.Lx, gf.Ly, gf.L, s);
+        tab[q] = GreenT<T>{(T)g.k2a, (T)g.omEa, (T)g.k2b, (T)g.omEb, g.kzero, g.same};
     }
+}
+
+// The plan's Green's table as doubles, [count][4] = (|k|², 1 - e^{-|k|L}, the
+// same for the partner), for stage-level tests of exactly what a solve reads.
+template <typename T>
+__global__ void k_green_dump(const GreenT<T>* __restrict__ tab, double* __restrict__ out, int count) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    const GreenT<T> g = tab[q];
+    out[4 * q + 0] = (double)g.k2a;
+    out[4 * q + 1] = (double)g.omEa;
+    out[4 * q + 2] = (double)g.k2b;
+    out[4 * q + 3] = (double)g.omEb;
 }
 
 // Vectorised contiguous copy global → shared staging (16-byte chunks when the
@@ -597,6 +569,10 @@ __global__ void __launch_bounds__(kMaxThreads, (min_blocks_xs<T, E, NS>()))
     const bool ok = mbar_wait_bounded(bar, 0, ctl.budget);
     if (!__syncthreads_and(ok)) {  // uniform exit: the copy did not arrive in time
         if (tid == 0) atomicExch(ctl.err, 1);
+        // A copy that was issued but is only late still targets this block's
+        // shared memory: keep the block resident (a second bounded wait) until
+        // it lands, so that it cannot write into memory given to another block.
+        if (!ctl.withhold) mbar_wait_bounded(bar, 0, ctl.budget);
         return;
     }
 

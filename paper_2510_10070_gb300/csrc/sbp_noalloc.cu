@@ -21,7 +21,6 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "../../include/sbp.h"
 #include "sbp_internal.h"
@@ -88,11 +87,65 @@ bool fft_plan(int n, FftPlan& P) {
     return true;
 }
 
-void twiddles(float* out, int count, double den) {
-    for (int k = 0; k < count; ++k) {
-        const double ang = 6.283185307179586476925286766559 * (double)k / den;
-        out[2 * k] = (float)std::cos(ang);
-        out[2 * k + 1] = (float)-std::sin(ang);
+// Where the per-call tables sit in the workspace (byte offsets) and what
+// they hold, for the table kernel below.
+struct TableArgs {
+    unsigned char* base;
+    size_t o_tx, o_ty, o_tz, o_t2, o_kz, o_c00;
+    int nx, ny, nz;
+    double Lz;
+};
+
+// Builds every table of a call on the device, in FP64, rounded once to the
+// float the kernels read: twiddles e^{-2πi k/n} for n = nx, ny, nz and
+// e^{-πi k/nz}; k_z,m² = (π m / Lz)² for m ≤ nz; and the FP64 k = 0 vertical
+// kernel c00_n = (1/2nz) [Lz²/2 + Σ_{m odd} (-2/k_z,m²) cos(π m n / nz)],
+// |n| < nz (Eq. Green's function regularized in Fourier at k = 0 with L = Lz,
+// inverse-transformed over the 2nz padded modes).  Blocks 0 .. 2nz-2 each
+// reduce one c00 entry over m (integer phase m·n mod 2nz, so the cosine
+// argument is exact); the remaining blocks write the twiddles and k_z².
+__global__ void __launch_bounds__(256) k_noalloc_tables(TableArgs A) {
+    __shared__ double red[256];
+    const int tid = threadIdx.x;
+    const int nc = 2 * A.nz - 1;
+    if ((int)blockIdx.x < nc) {
+        const int n = (int)blockIdx.x - (A.nz - 1);
+        const int M = 2 * A.nz;
+        const double pi_over_lz = 3.141592653589793238462643383279 / A.Lz;
+        double acc = 0.0;
+        for (int m = -A.nz + 1 + 2 * tid; m < A.nz; m += 2 * blockDim.x) {  // odd m in [-nz, nz)
+            long long ph = ((long long)m * n) % M;
+            if (ph < 0) ph += M;
+            const double kz = pi_over_lz * (double)m;
+            acc += (-2.0 / (kz * kz)) * cospi((double)ph / (double)A.nz);
+        }
+        red[tid] = acc;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (tid < w) red[tid] += red[tid + w];
+            __syncthreads();
+        }
+        if (tid == 0)
+            reinterpret_cast<double*>(A.base + A.o_c00)[n + A.nz - 1] = (0.5 * A.Lz * A.Lz + red[0]) / (double)M;
+        return;
+    }
+    // twiddles and k_z²: one entry per thread over the remaining blocks
+    const int i = ((int)blockIdx.x - nc) * blockDim.x + tid;
+    auto tw = [&](size_t off, int k, int count, double den) {
+        if (k >= count) return;
+        double sn, cs;
+        sincospi(2.0 * (double)k / den, &sn, &cs);
+        float* out = reinterpret_cast<float*>(A.base + off);
+        out[2 * k] = (float)cs;
+        out[2 * k + 1] = (float)-sn;
+    };
+    tw(A.o_tx, i, A.nx, A.nx);
+    tw(A.o_ty, i, A.ny, A.ny);
+    tw(A.o_tz, i, A.nz, A.nz);
+    tw(A.o_t2, i, A.nz, 2.0 * A.nz);
+    if (i <= A.nz) {
+        const double kz = 3.141592653589793238462643383279 * (double)i / A.Lz;
+        reinterpret_cast<float*>(A.base + A.o_kz)[i] = (float)(kz * kz);
     }
 }
 
@@ -162,7 +215,6 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     const size_t oTs = take((size_t)xblocks * sizeof(double));
     const size_t oVk = take((size_t)nz * sizeof(double));
     const size_t oGr = take((size_t)h * ny * sizeof(GreenT<float>));
-    const size_t oHostEnd = oKz + (nz + 1) * sizeof(float);  // tables copied from the host: [oTx, oHostEnd)
     if (off > kScratchBytes) return SBP_ERR_SCRATCH_LIMIT;
 
     void* base_v = nullptr;
@@ -171,36 +223,23 @@ extern "C" sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, doubl
     unsigned char* base = static_cast<unsigned char*>(base_v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    // ---- tables: twiddles and k_z² (host FP64, rounded), and the k = 0
-    // vertical kernel c00 (FP64, Lz = L: Ĝ(0,0) = Lz²/2, Ĝ(0,m) = ((-1)^m - 1)/k_z²)
-    std::vector<unsigned char> host(oHostEnd - oTx, 0);
-    twiddles(reinterpret_cast<float*>(host.data() + (oTx - oTx)), nx, nx);
-    twiddles(reinterpret_cast<float*>(host.data() + (oTy - oTx)), ny, ny);
-    twiddles(reinterpret_cast<float*>(host.data() + (oTz - oTx)), nz, nz);
-    twiddles(reinterpret_cast<float*>(host.data() + (oT2 - oTx)), nz, 2.0 * nz);
+    // ---- tables: built on the device by one kernel (no host staging, no copies)
     {
-        float* kz2 = reinterpret_cast<float*>(host.data() + (oKz - oTx));
-        for (int m = 0; m <= nz; ++m) {
-            const double kz = M_PI * (double)m / Lz;
-            kz2[m] = (float)(kz * kz);
-        }
-    }
-    std::vector<double> c00(2 * (size_t)nz - 1, 0.0);
-    for (int n = -(nz - 1); n <= nz - 1; ++n) {
-        double acc = 0.5 * Lz * Lz;
-        for (int m = -nz; m < nz; ++m) {
-            if ((m & 1) == 0) continue;
-            const double kz = M_PI * (double)m / Lz;
-            const long long ph = ((long long)m * n) % (2 * nz);
-            acc += (-2.0 / (kz * kz)) * std::cos(M_PI * (double)ph / (double)nz);
-        }
-        c00[n + nz - 1] = acc / (2.0 * nz);
-    }
-    if (cudaMemcpyAsync(base + oTx, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(base + oC00, c00.data(), c00.size() * sizeof(double), cudaMemcpyHostToDevice, st) !=
-            cudaSuccess) {
-        cudaGetLastError();
-        return SBP_ERR_CUDA;
+        TableArgs ta;
+        ta.base = base;
+        ta.o_tx = oTx;
+        ta.o_ty = oTy;
+        ta.o_tz = oTz;
+        ta.o_t2 = oT2;
+        ta.o_kz = oKz;
+        ta.o_c00 = oC00;
+        ta.nx = nx;
+        ta.ny = ny;
+        ta.nz = nz;
+        ta.Lz = Lz;
+        const int entries = std::max(std::max(nx, ny), nz + 1);
+        const int blocks = (2 * nz - 1) + (entries + 255) / 256;
+        k_noalloc_tables<<<blocks, 256, 0, st>>>(ta);
     }
 
     const int lim = (int)kSmemLimit;

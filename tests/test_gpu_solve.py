@@ -124,6 +124,60 @@ def test_in_place_and_batched_match_single(sbp, dtype):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
+def test_batched_in_place_first_call(sbp, dtype):
+    # An uneven batch solved in place (phi[i] is rho[i]) on the executor's
+    # FIRST call, which times its candidate graphs: every box must come out
+    # solved exactly once, bit for bit as sbp_solve gives it, and within the
+    # oracle's bars.  Again after an option change drops the cached graph.
+    import torch
+
+    shapes = [(64, 64, 32), (32, 32, 16), (48, 24, 12), (96, 64, 48), (16, 16, 8)]
+    rng = np.random.default_rng(23)
+    boxes = [W.Box(nx, ny, nz, 2.0, 3.0, 1.5, q=1.5 if i % 2 == 0 else 1.0) for i, (nx, ny, nz) in enumerate(shapes)]
+    plans = [_plan(sbp, b, dtype) for b in boxes]
+    for ts in ([0.4, 2.5, -1.3, 3.9, 7.1], [6.2, -0.5, 1.7, 0.0, 2.2]):
+        rho_np = [rng.standard_normal((b.nz, b.ny, b.nx)) + 0.3 for b in boxes]
+        bufs = [to_dev(r, dtype) for r in rho_np]
+        singles = [plans[i].solve(to_dev(rho_np[i], dtype), t=ts[i]) for i in range(len(plans))]
+        sbp.solve_batched(plans, bufs, bufs, ts)
+        torch.cuda.synchronize()
+        for i in range(len(plans)):
+            assert torch.equal(bufs[i], singles[i]), (i, ts)
+        want = O.solve(as_input(rho_np[3], dtype), _params(boxes[3]), ts[3])
+        assert rel_l2(bufs[3].double().cpu().numpy(), want) <= TOL[dtype]
+        plans[2].set_option(sbp.Option.Z_VARIANT, 0)  # drops the executor: the next call tunes again
+
+
+def test_batched_rejects_aliasing_across_boxes(sbp):
+    import torch
+
+    box = W.Box(16, 16, 8, 1.0, 1.0, 1.0)
+    plans = [_plan(sbp, box, 1) for _ in range(2)]
+    n = box.nz * box.ny * box.nx
+    buf = torch.zeros(3 * n, dtype=torch.float32, device="cuda")
+    v = [buf[i * n:(i + 1) * n].view(box.nz, box.ny, box.nx) for i in range(3)]
+    # box 0 writes what box 1 reads
+    with pytest.raises(sbp.SbpError) as err:
+        sbp.solve_batched(plans, [v[0], v[1]], [v[1], v[2]], [0.1, 0.2])
+    assert err.value.status == sbp.Status.INVALID_ARG
+    # two boxes writing the same output
+    with pytest.raises(sbp.SbpError) as err:
+        sbp.solve_batched(plans, [v[0], v[1]], [v[2], v[2]], [0.1, 0.2])
+    assert err.value.status == sbp.Status.INVALID_ARG
+    # a partial overlap between boxes
+    shifted = buf[n // 2:n // 2 + n].view(box.nz, box.ny, box.nx)
+    with pytest.raises(sbp.SbpError):
+        sbp.solve_batched(plans, [v[0], v[2]], [v[1], shifted], [0.1, 0.2])
+    # two boxes reading the same density is fine
+    out = [torch.empty_like(v[0]), torch.empty_like(v[0])]
+    v[0].copy_(torch.randn_like(v[0]))
+    sbp.solve_batched(plans, [v[0], v[0]], out, [0.1, 0.2])
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], plans[0].solve(v[0], t=0.1))
+    assert torch.equal(out[1], plans[1].solve(v[0], t=0.2))
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
 def test_batched_uneven_boxes_repeated_calls(sbp, dtype):
     # cached executor: later calls change only the shear times
     import torch

@@ -127,12 +127,22 @@ def test_x_inverse(sbp, shape, dtype):
     assert rel_l2(out.double().cpu().numpy(), want) <= STAGE_TOL[dtype]
 
 
+def _within_f32_ulp(got, want):
+    """Every entry is the FP64 value rounded to float, give or take one float ulp."""
+    w32 = want.astype(np.float32)
+    return bool(np.all(np.abs(got - w32.astype(np.float64)) <= np.spacing(np.abs(w32)).astype(np.float64)))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("t", [0.0, 0.7, 5.0, -1.1])
-@pytest.mark.parametrize("shape", [(8, 6, 4), (96, 64, 8), (256, 256, 2)])
-def test_green_table(sbp, shape, t):
+@pytest.mark.parametrize("shape", [(8, 6, 4), (96, 64, 8), (256, 256, 2), (192, 128, 2)])
+def test_green_table(sbp, shape, t, dtype):
+    # The table a solve reads: |k|² and 1 - e^{-kL} of every stored mode and
+    # of its Hermitian partner, tabulated in FP64 (an FP32 plan stores them
+    # rounded once to float) against the oracle's sheared wave-vectors.
     nx, ny, nz = shape
     h = nx // 2 + 1
-    plan = _plan(sbp, shape, 0)
+    plan = _plan(sbp, shape, dtype)
     import torch
 
     out = torch.zeros((ny, h, 4), dtype=torch.float64, device="cuda")
@@ -142,12 +152,18 @@ def test_green_table(sbp, shape, t):
     k1, k2, is0 = O.mode_wavenumbers(nx, ny, L[0], L[1], s)
     k1, k2, is0 = k1[:, :h], k2[:, :h], is0[:, :h]
     Lz = L[2]
-    assert np.allclose(got[..., 0], k1 ** 2, rtol=1e-14, atol=1e-14)
-    assert np.allclose(got[..., 2], k2 ** 2, rtol=1e-14, atol=1e-14)
-    om1 = np.where(is0, 0.0, 1.0 - np.exp(-k1 * Lz))
-    om2 = np.where(is0, got[..., 3], 1.0 - np.exp(-k2 * Lz))
-    assert np.allclose(got[..., 1], om1, rtol=1e-14, atol=1e-15)
-    assert np.allclose(got[..., 3], om2, rtol=1e-14, atol=1e-15)
+    om1 = np.where(is0, 0.0, -np.expm1(-k1 * Lz))
+    om2 = np.where(is0, got[..., 3], -np.expm1(-k2 * Lz))
+    if dtype == 0:
+        assert np.allclose(got[..., 0], k1 ** 2, rtol=1e-14, atol=1e-14)
+        assert np.allclose(got[..., 2], k2 ** 2, rtol=1e-14, atol=1e-14)
+        assert np.allclose(got[..., 1], om1, rtol=1e-14, atol=1e-15)
+        assert np.allclose(got[..., 3], om2, rtol=1e-14, atol=1e-15)
+    else:
+        assert _within_f32_ulp(got[..., 0], k1 ** 2)
+        assert _within_f32_ulp(got[..., 2], k2 ** 2)
+        assert _within_f32_ulp(got[..., 1], om1)
+        assert _within_f32_ulp(got[..., 3], om2)
     # the partner differs only on the Nyquist planes, and only when sheared
     differ = np.abs(got[..., 0] - got[..., 2]) > 0
     if s == 0.0:

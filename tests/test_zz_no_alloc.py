@@ -9,7 +9,8 @@ already run."""
 import numpy as np
 import pytest
 
-from gpu_helpers import TOL, rel_l2, to_dev
+import oracle as O
+from gpu_helpers import TOL, as_input, rel_l2, to_dev
 from paper_2510_10070_gb300 import workloads as W
 
 
@@ -41,6 +42,10 @@ def test_noalloc_matches_plan_solve_twice(sbp, box):
         torch.cuda.synchronize()
         assert torch.isfinite(got).all(), call
         assert rel_l2(got.double().cpu().numpy(), want.double().cpu().numpy()) <= TOL[1], (call, t)
+        if box.cells <= 64 ** 3:  # and against the FP64 oracle where it is quick
+            p = O.SolveParams(box.Lx, box.Ly, box.Lz, q=box.q, Omega=box.Omega, G=box.G)
+            ref = O.solve(as_input(rho.double().cpu().numpy(), 1), p, t)
+            assert rel_l2(got.double().cpu().numpy(), ref) <= TOL[1], (call, t)
 
 
 @pytest.mark.gpu
