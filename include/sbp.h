@@ -71,7 +71,10 @@ typedef enum {
     SBP_STAGE_Y_INVERSE = 3,
     SBP_STAGE_X_INVERSE = 4,
     SBP_STAGE_GREEN_TABLE = 5,
-    SBP_STAGE_GREEN_FILL = 6
+    SBP_STAGE_GREEN_FILL = 6,
+    SBP_STAGE_SWEEP_FORWARD = 7,
+    SBP_STAGE_SWEEP_MIDDLE = 8,
+    SBP_STAGE_SWEEP_INVERSE = 9
 } sbp_stage;
 
 /*
@@ -97,9 +100,10 @@ sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz,
  * convolution Φ = 4πG F⁻¹(Ĝ^L·ρ̂).  rho: device input (see conventions);
  * phi: device output of the same shape and type.  phi == rho (in place) is
  * allowed; any other overlap returns SBP_ERR_INVALID_ARG.  Both pointers must
- * be 16-byte aligned.  Runs five kernels on `stream`: x forward (real to half
- * spectrum), y forward, the fused padded z pass (Green's multiply), y inverse,
- * x inverse.
+ * be 16-byte aligned.  Runs on `stream` either three kernels (the three
+ * sweeps of SBP_OPT_SCHEDULE, where they apply) or five: x forward (real to
+ * half spectrum), y forward, the fused padded z pass (Green's multiply),
+ * y inverse, x inverse.
  */
 sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* stream);
 
@@ -213,7 +217,22 @@ enum {
      * itself: its first call times the graphs with and without chunks of
      * about 8 MiB of spectrum (SBP_BATCH_CHUNK=0/1 in the environment forces
      * one).  Results are identical either way. */
-    SBP_OPT_XY_CHUNK = 9
+    SBP_OPT_XY_CHUNK = 9,
+    /* Schedule of the solves (same result to rounding, different speed).
+     * 0 (default): automatic; 1: five passes (x, y, z, y, x); 2: three sweeps
+     * over the half spectrum, with the y transform's two radix stages fused
+     * into the passes around the z pass (x + first y stage, second y stage +
+     * padded z pass + first inverse y stage, second inverse y stage + x).
+     * The three sweeps serve SBP_F32 plans in the periodic frame with the VGF
+     * method and 2·nz padding for the box shapes built for them (nx, ny, nz)
+     * = (32, 32, 32), (64, 64, 32), (64, 64, 64), (128, 128, 64),
+     * (128, 128, 128), (192, 192, 96), (256, 256, 64), (256, 256, 128);
+     * automatic takes them there unless a five-pass variant was asked for
+     * (SBP_OPT_XY_PASSES, SBP_OPT_Z_VARIANT, SBP_OPT_Y_TMA or
+     * SBP_OPT_XY_CHUNK set to a value other than 0).  2 returns
+     * SBP_ERR_UNSUPPORTED_SIZE where the three sweeps do not apply.  The
+     * stages of sbp_run_stage are the five-pass kernels in every schedule. */
+    SBP_OPT_SCHEDULE = 10
 };
 
 /* sbp_fill_ghosts — vertical ghost layers of a solution (Sect. 2.4, last
@@ -295,6 +314,19 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  *                         (an SBP_F32 plan holds the FP64 values rounded once
  *                         to float), widened to double.
  * The FP32 mean-mode side path is not part of any single stage.
+ *
+ * The three sweeps of a plan whose solves run them (SBP_OPT_SCHEDULE), on the
+ * plan's own workspace in its internal layout (else SBP_ERR_INVALID_ARG):
+ *   SBP_STAGE_SWEEP_FORWARD: in = real [nz][ny][nx]; out ignored (may be
+ *                         NULL).  Fills the Green's table for time t and the
+ *                         plane sums, and leaves the x transform and the
+ *                         first y stage in the workspace.
+ *   SBP_STAGE_SWEEP_MIDDLE:  in and out ignored.  The second y stage, the
+ *                         padded z pass with the Green's multiply and the
+ *                         first inverse y stage, in place, plus the FP64
+ *                         mean mode.
+ *   SBP_STAGE_SWEEP_INVERSE: in ignored; out = real [nz][ny][nx].
+ * Run in this order they give sbp_solve's result bit for bit.
  */
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream);
 
@@ -329,6 +361,16 @@ sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, doubl
 sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz,
                              double q, double Omega, double G,
                              const float* rho, float* phi, double t, void* stream);
+
+/* sbp_plan_query — what a plan's solves do now (not part of the paper's
+ * method; for callers that report or schedule work).  what:
+ *   SBP_QUERY_SCHEDULE (1): 1 = five passes, 2 = three sweeps (see
+ *       SBP_OPT_SCHEDULE), after the automatic choice;
+ *   SBP_QUERY_LAUNCHES_PER_SOLVE (2): kernels one sbp_solve launches.
+ * *value receives the answer.  NULL plan or value, or an unknown `what`:
+ * SBP_ERR_INVALID_ARG. */
+enum { SBP_QUERY_SCHEDULE = 1, SBP_QUERY_LAUNCHES_PER_SOLVE = 2 };
+sbp_status sbp_plan_query(sbp_plan p, int what, double* value);
 
 /* sbp_version — library version string. */
 const char* sbp_version(void);

@@ -82,6 +82,14 @@ struct sbp_plan_s {
     // (as printed), 2 = SASHA with the vertex at z0/2
     int method = 0;
     int chunk = 0;  // planes per x/y chunk of a single solve (SBP_OPT_XY_CHUNK; 0: whole box)
+    // explicitly requested five-pass variants (SBP_OPT_XY_PASSES, SBP_OPT_Z_VARIANT, SBP_OPT_Y_TMA)
+    int xy_req = 0, z_req = 0, ytma_req = 0;
+    // schedule (SBP_OPT_SCHEDULE): 0 = automatic, 1 = five passes, 2 = three sweeps
+    int schedule = 0;
+    bool sweep = false;              // solves run the three-sweep kernels
+    SweepKernels sk;
+    int sweep_green_blocks = 0;
+    SweepBox* sweep_box = nullptr;   // this plan's device descriptor (in `tables`)
     // z-pass geometry: stored columns per row, rows per plane, row pitch
     int zh = 0, zrows = 0, zpitch = 0;
     // physical frame (SBP_OPT_FRAME = 1): y-first passes with the mapping of Sect. 2.1
@@ -517,11 +525,13 @@ sbp_status upload_tables(sbp_plan_s* p) {
     const size_t o_ptab = take(ptab.size() * sizeof(T));
     const size_t o_c00 = take((2 * (size_t)p->nz) * sizeof(double));
     const int ry_tiles = (p->nx / 2 + ypass_cols(p->ny, !f32) - 1) / ypass_cols(p->ny, !f32) * p->nz;
-    const size_t o_ts = take((size_t)std::max(tiles, ry_tiles) * sizeof(double));
+    const int sweep_tiles = p->nz * std::max(1, sweep_ra(p->ny) > 0 ? p->ny / sweep_ra(p->ny) : 1);
+    const size_t o_ts = take((size_t)std::max(std::max(tiles, ry_tiles), sweep_tiles) * sizeof(double));
     const size_t o_vk0 = take((size_t)p->nz * sizeof(double));
     const size_t o_err = take(sizeof(int));
     const size_t o_side = take((size_t)p->nz * 2 * p->ny * sizeof(T));
     const size_t o_green = take(std::max((size_t)p->h * p->ny, (size_t)p->nx * (p->ny / 2 + 1)) * sizeof(GreenT<T>));
+    const size_t o_sbox = take(sizeof(SweepBox));
     p->tables_bytes = off;
     if (cudaMalloc(&p->tables, off) != cudaSuccess) {
         cudaGetLastError();
@@ -542,8 +552,27 @@ sbp_status upload_tables(sbp_plan_s* p) {
     p->tw_M4 = base + o_twM4;
     p->paper_tab = base + o_ptab;
     p->green = base + o_green;
+    p->sweep_box = reinterpret_cast<SweepBox*>(base + o_sbox);
 
     std::vector<unsigned char> host(off, 0);
+    {
+        // the plan's descriptor for the three-sweep kernels (FP32 plans; rho,
+        // phi and the shear parameter come with each launch)
+        SweepBox d;
+        std::memset(&d, 0, sizeof(d));
+        d.S = reinterpret_cast<cpx<float>*>(p->W);
+        d.green = reinterpret_cast<GreenT<float>*>(p->green);
+        d.tile_sums = p->tile_sums;
+        d.vk0 = p->vk0;
+        d.c00 = p->c00;
+        d.Lx = p->Lx;
+        d.Ly = p->Ly;
+        d.L = p->alpha * p->Lz;
+        d.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * 2.0 * p->nz);
+        d.kzc = (M_PI / p->Lz) * (M_PI / p->Lz);
+        d.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
+        std::memcpy(host.data() + o_sbox, &d, sizeof(d));
+    }
     auto put_cpx = [&](size_t o, const std::vector<double>& v) {
         T* d = reinterpret_cast<T*>(host.data() + o);
         for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
@@ -1006,9 +1035,81 @@ bool configure_frame(sbp_plan_s* p, int frame) {
     return true;
 }
 
+// Schedule of the solves (SBP_OPT_SCHEDULE).  The three-sweep kernels serve
+// FP32 plans in the periodic frame with the VGF method and 2·nz padding, for
+// the box shapes they are built for, unless a five-pass variant was requested
+// (SBP_OPT_XY_PASSES, SBP_OPT_Z_VARIANT, SBP_OPT_Y_TMA or SBP_OPT_XY_CHUNK set
+// to a non-default value).  Returns false when schedule 2 is asked for and
+// unavailable (the plan then keeps five passes).
+bool configure_sweep(sbp_plan_s* p) {
+    p->sweep = false;
+    if (p->schedule == 1) return true;
+    const bool eligible = !f64_of(p) && p->frame == 0 && p->method == 0 && p->pad == 2 &&
+                          (p->schedule == 2 || (p->xy_req == 0 && p->z_req == 0 && p->ytma_req == 0 && p->chunk == 0));
+    const SweepKernels k = eligible ? sweep_kernels_for(p->nx, p->ny, p->nz) : SweepKernels{};
+    if (!k.fwd) return p->schedule != 2;
+    if (k.smem_ac > kSmemBudget || k.smem_b > kSmemBudget) return p->schedule != 2;
+    const void* fns[3] = {reinterpret_cast<const void*>(k.fwd), reinterpret_cast<const void*>(k.mid),
+                          reinterpret_cast<const void*>(k.inv)};
+    for (const void* f : fns) {
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) != cudaSuccess) {
+            cudaGetLastError();
+            return p->schedule != 2;
+        }
+    }
+    p->sk = k;
+    p->sweep_green_blocks = (p->h * p->ny + k.nta - 1) / k.nta;
+    p->sweep = true;
+    return true;
+}
+
+SweepArgs sweep_args(const sbp_plan_s* p) {
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.boxes = p->sweep_box;
+    a.twx = static_cast<const cpx<float>*>(p->tw_x);
+    a.twy = static_cast<const cpx<float>*>(p->tw_y);
+    a.twM = static_cast<const cpx<float>*>(p->tw_M);
+    a.green_blocks = p->sweep_green_blocks;
+    return a;
+}
+
+// The three sweeps of one solve (see sbp_sweep.cuh), `nbox` boxes of the
+// plan's shape at once when `a.boxes` holds their descriptors.
+sbp_status launch_sweep(const sbp_plan_s* p, const SweepArgs& a, int nbox, cudaStream_t st) {
+    const SweepKernels& k = p->sk;
+    const int ablocks = (p->nz / k.za) * k.rb;
+    k.fwd<<<dim3((unsigned)(a.green_blocks + ablocks), (unsigned)nbox), k.nta, k.smem_ac, st>>>(a);
+    k.mid<<<dim3((unsigned)(k.ra * k.nga + 1), (unsigned)nbox), k.ntb, k.smem_b, st>>>(a);
+    k.inv<<<dim3((unsigned)ablocks, (unsigned)nbox), k.nta, k.smem_ac, st>>>(a);
+    return launch_status();
+}
+
+sbp_status solve_sweep(const sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
+                       const double* s_dev) {
+    SweepArgs a = sweep_args(p);
+    a.rho = static_cast<const float*>(rho);
+    a.phi = static_cast<float*>(phi);
+    a.s = shear_s(p, t);
+    a.s_dev = s_dev;
+    return launch_sweep(p, a, 1, st);
+}
+
+// Kernels one solve launches (solve_t's dispatch; chunk < 0: the plan's own).
+int launches_per_solve(const sbp_plan_s* p, int chunk) {
+    if (chunk < 0) chunk = p->chunk;
+    if (p->sweep && chunk <= 0) return 3;
+    const int sasha = p->method != 0 ? 1 : 0;
+    if (p->frame) return 5 + sasha;
+    if (p->xy_fused) return 3;
+    if (chunk > 0 && chunk < p->nz) return 1 + sasha + 4 * ((p->nz + chunk - 1) / chunk);
+    return 5 + sasha;
+}
+
 template <typename T>
 sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
                    const double* s_dev = nullptr, int chunk = -1) {
+    if (p->sweep && chunk <= 0) return solve_sweep(p, rho, phi, t, st, s_dev);
     if (p->frame) return solve_physical_t<T>(p, rho, phi, t, st, s_dev);
     if (p->xy_fused) return solve_fused_t<T>(p, rho, phi, t, st, s_dev);
     if (chunk < 0) chunk = p->chunk;
@@ -1104,7 +1205,7 @@ void drop_executors(const sbp_plan_s* p) {
 // Planes per x/y chunk that keep a chunk's half spectrum near 8 MiB (0 when
 // the whole box is already that small or the plan takes other passes).
 int auto_chunk(const sbp_plan_s* p) {
-    if (p->frame || p->xy_fused) return 0;
+    if (p->frame || p->xy_fused || p->sweep) return 0;
     const size_t plane = (size_t)p->ny * p->pitch * 2 * p->rsize;
     const int c = (int)std::max<size_t>(1, ((size_t)8 << 20) / plane);
     return c >= p->nz ? 0 : c;
@@ -1432,6 +1533,7 @@ sbp_status sbp_plan_create(sbp_plan* out, int nx, int ny, int nz, double Lx, dou
     } else {
         configure_ytma<float>(p, true);
     }
+    configure_sweep(p);
     *out = p;
     return SBP_OK;
 }
@@ -1595,10 +1697,52 @@ const char* sbp_status_string(sbp_status s) {
     return "unknown status";
 }
 
+static sbp_status set_option_impl(sbp_plan p, int option, double value);
+
 sbp_status sbp_plan_set_option(sbp_plan p, int option, double value) {
     if (!p || !std::isfinite(value)) return SBP_ERR_INVALID_ARG;
+    if (option == SBP_OPT_SCHEDULE) {
+        const int v = (int)value;
+        if ((double)v != value || v < 0 || v > 2) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        drop_executors(p);
+        const int old = p->schedule;
+        p->schedule = v;
+        if (!configure_sweep(p)) {
+            p->schedule = old;
+            configure_sweep(p);
+            return SBP_ERR_UNSUPPORTED_SIZE;
+        }
+        return SBP_OK;
+    }
+    const sbp_status st = set_option_impl(p, option, value);
+    if (st == SBP_OK) {
+        // the requested five-pass variants, and the frame, method and
+        // truncation, decide whether the solves keep the three-sweep kernels
+        if (option == SBP_OPT_XY_PASSES) p->xy_req = (int)value;
+        if (option == SBP_OPT_Z_VARIANT) p->z_req = (int)value;
+        if (option == SBP_OPT_Y_TMA) p->ytma_req = (int)value;
+        if (option == SBP_OPT_XY_PASSES || option == SBP_OPT_Z_VARIANT || option == SBP_OPT_Y_TMA ||
+            option == SBP_OPT_XY_CHUNK || option == SBP_OPT_FRAME || option == SBP_OPT_METHOD ||
+            option == SBP_OPT_TRUNCATION) {
+            DeviceGuard g(p->device);
+            if (!g.ok) return SBP_ERR_CUDA;
+            if (!configure_sweep(p)) {  // a forced three-sweep schedule no longer applies
+                p->schedule = 0;
+                configure_sweep(p);
+            }
+        }
+    }
+    return st;
+}
+
+static sbp_status set_option_impl(sbp_plan p, int option, double value) {
     if (option == SBP_OPT_Y_TMA || option == SBP_OPT_XY_PASSES || option == SBP_OPT_Z_VARIANT ||
-        option == SBP_OPT_TRUNCATION || option == SBP_OPT_FRAME || option == SBP_OPT_METHOD) {
+        option == SBP_OPT_TRUNCATION || option == SBP_OPT_FRAME || option == SBP_OPT_METHOD ||
+        option == SBP_OPT_XY_CHUNK) {
         // captured batch graphs hold the old kernels and arguments
         DeviceGuard g(p->device);
         if (!g.ok) return SBP_ERR_CUDA;
@@ -1707,7 +1851,29 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype, int*
 }
 
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream) {
-    if (!p || !out || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (!p || !std::isfinite(t)) return SBP_ERR_INVALID_ARG;
+    if (stage >= SBP_STAGE_SWEEP_FORWARD && stage <= SBP_STAGE_SWEEP_INVERSE) {
+        if (!p->sweep) return SBP_ERR_INVALID_ARG;
+        if (stage == SBP_STAGE_SWEEP_FORWARD && (!in || !aligned16(in))) return SBP_ERR_INVALID_ARG;
+        if (stage == SBP_STAGE_SWEEP_INVERSE && (!out || !aligned16(out))) return SBP_ERR_INVALID_ARG;
+        DeviceGuard g(p->device);
+        if (!g.ok) return SBP_ERR_CUDA;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        SweepArgs a = sweep_args(p);
+        a.rho = static_cast<const float*>(in != nullptr ? in : p->W);  // non-null: the single-box form
+        a.phi = static_cast<float*>(out);
+        a.s = shear_s(p, t);
+        const SweepKernels& k = p->sk;
+        const int ablocks = (p->nz / k.za) * k.rb;
+        if (stage == SBP_STAGE_SWEEP_FORWARD)
+            k.fwd<<<dim3((unsigned)(a.green_blocks + ablocks)), k.nta, k.smem_ac, st>>>(a);
+        else if (stage == SBP_STAGE_SWEEP_MIDDLE)
+            k.mid<<<dim3((unsigned)(k.ra * k.nga + 1)), k.ntb, k.smem_b, st>>>(a);
+        else
+            k.inv<<<dim3((unsigned)ablocks), k.nta, k.smem_ac, st>>>(a);
+        return launch_status();
+    }
+    if (!out) return SBP_ERR_INVALID_ARG;
     if (p->frame != 0 || p->method != 0) return SBP_ERR_INVALID_ARG;  // the stages are the VGF periodic-frame passes
     if (stage < SBP_STAGE_X_FORWARD || stage > SBP_STAGE_GREEN_FILL) return SBP_ERR_INVALID_ARG;
     if (stage != SBP_STAGE_GREEN_TABLE && stage != SBP_STAGE_GREEN_FILL && !in) return SBP_ERR_INVALID_ARG;
@@ -1722,6 +1888,19 @@ sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, doubl
                      : launch_stage<float>(p, stage, in, out, t, st, false);
 }
 
-const char* sbp_version(void) { return "sbp 0.1.0 (sm_103a)"; }
+sbp_status sbp_plan_query(sbp_plan p, int what, double* value) {
+    if (!p || !value) return SBP_ERR_INVALID_ARG;
+    if (what == SBP_QUERY_SCHEDULE) {
+        *value = p->sweep ? 2.0 : 1.0;
+        return SBP_OK;
+    }
+    if (what == SBP_QUERY_LAUNCHES_PER_SOLVE) {
+        *value = (double)launches_per_solve(p, -1);
+        return SBP_OK;
+    }
+    return SBP_ERR_INVALID_ARG;
+}
+
+const char* sbp_version(void) { return "sbp 0.2.0 (sm_103a)"; }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include "sbp_kernels.cuh"
 #include "sbp_force.cuh"
 #include "sbp_remap.cuh"
+#include "sbp_sweep.cuh"
 #include "sbp_xy.cuh"
 
 namespace sbp {
@@ -232,6 +233,44 @@ inline RemapKernels<T> remap_kernels_for(int nx, int ny) {
     r.rows_inv = x.rows_inv;
     r.rows_E = x.rows_E;
     return r;
+}
+
+// Three-sweep kernels (FP32) for the box shapes (NX, NY, NZ) built below.
+struct SweepKernels {
+    void (*fwd)(SweepArgs) = nullptr;
+    void (*mid)(SweepArgs) = nullptr;
+    void (*inv)(SweepArgs) = nullptr;
+    int nta = 0, ntb = 0, za = 0, ra = 0, rb = 0, nga = 0;
+    size_t smem_ac = 0, smem_b = 0;
+};
+#define SBP_SWEEP_LIST(X) X(32, 32, 32) X(64, 64, 32) X(64, 64, 64) X(128, 128, 64) X(128, 128, 128) \
+    X(192, 192, 96) X(256, 256, 64) X(256, 256, 128)
+#define SBP_DECLARE_SWEEP(NX, NY, NZ) SweepKernels sweep_##NX##_##NY##_##NZ();
+SBP_SWEEP_LIST(SBP_DECLARE_SWEEP)
+#define SBP_DEFINE_SWEEP(NX, NY, NZ)                   \
+    SweepKernels sweep_##NX##_##NY##_##NZ() {          \
+        using SH = SweepShape<NX, NY, NZ>;             \
+        SweepKernels k;                                \
+        k.fwd = k3_forward<NX, NY, NZ>;                \
+        k.mid = k3_middle<NX, NY, NZ>;                 \
+        k.inv = k3_inverse<NX, NY, NZ>;                \
+        k.nta = SH::NTA;                               \
+        k.ntb = SH::NTB;                               \
+        k.za = SH::ZA;                                 \
+        k.ra = SH::RA;                                 \
+        k.rb = SH::RB;                                 \
+        k.nga = SH::NGA;                               \
+        k.smem_ac = SH::smem_ac;                       \
+        k.smem_b = SH::smem_b;                         \
+        return k;                                      \
+    }
+
+inline SweepKernels sweep_kernels_for(int nx, int ny, int nz) {
+#define SBP_MATCH_SWEEP(NX, NY, NZ) \
+    if (nx == NX && ny == NY && nz == NZ) return sweep_##NX##_##NY##_##NZ();
+    SBP_SWEEP_LIST(SBP_MATCH_SWEEP)
+#undef SBP_MATCH_SWEEP
+    return SweepKernels{};
 }
 
 // True when length n has static kernels for type T.

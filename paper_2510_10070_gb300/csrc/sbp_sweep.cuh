@@ -1,0 +1,446 @@
+// sbp_sweep.cuh — the FP32 solve in three sweeps over the half spectrum.
+//
+// The y transform (length NY = RA·RB) is split into its two Stockham stages
+// and each stage is fused into a neighbouring pass, so that a solve reads
+// and writes the half spectrum once per pass and makes three passes instead
+// of five (Sect. 2.4: the transform and the Green's multiply per column;
+// here the transposes are the pass boundaries in HBM):
+//
+//   pass A (k3_forward): per (plane group, j ∈ [0, RB)): the real rows
+//       y = j + RB·r (r < RA) of ZA planes are transformed along x (two rows
+//       per complex FFT, Hermitian split on shuffles), then for every (z, a)
+//       the radix-RA stage over r is applied; output k ∈ [0, RA) is stored at
+//       S[k][a][j][z].  The first blocks of the grid fill the Green's table.
+//   pass B (k3_middle): per (k, group of AG columns a): twiddle ω_NY^{k·j}
+//       and the radix-RB stage over j give the full y spectrum at
+//       b = k + RA·r'; each (b, a) column then takes the padded length-2NZ z
+//       transform, the multiply by 4πG/(NX·NY·2NZ)·Ĝ_eff and the truncated
+//       inverse (as k_z_padded); the inverse y transform's first stage
+//       (radix RB over r', on the conjugated data, no twiddle) follows and
+//       output k' is stored at S[k][a][k'][z], in place.  One extra block per
+//       box convolves the FP64 plane sums with the k = 0 kernel.
+//   pass C (k3_inverse): per (plane group, j): twiddle ω_NY^{j·k} and the
+//       radix-RA stage over k give rows y = j + RB·r of the (conjugated)
+//       inverse y transform; the x inverse (Hermitian merge, c2r) follows and
+//       the FP64 mean mode is added as a double-float pair.
+//
+// The half spectrum S is [RA][NX/2+1][RB][NZ] complex: pass B's tile of one
+// (k, a) is RB·NZ contiguous values, and passes A and C touch ZA consecutive
+// z of every (k, a, j).
+//
+// Every kernel serves a group of boxes of the same shape: blockIdx.y picks
+// the box's descriptor (pointers, shear parameter, physical constants).
+#pragma once
+
+#include "sbp_kernels.cuh"
+
+namespace sbp {
+
+// Radix of the y stage fused into the x passes (RA) for a length NY; the
+// other stage (pass B) has radix NY / RA.  0: no split built for NY.
+__host__ __device__ constexpr int sweep_ra(int NY) {
+    return NY == 32 ? 4 : NY == 64 ? 8 : NY == 96 ? 12 : NY == 128 ? 16 : NY == 192 ? 12 : NY == 256 ? 16 : 0;
+}
+
+__host__ __device__ constexpr int sweep_stage_pitch(int need, int ZA) {
+    // plane stride of the staging buffer: at least `need`, and ≡ 16/ZA (mod 16)
+    // (odd for ZA ≥ 16) so that the ZA planes of one warp access fall in
+    // different banks
+    const int q = ZA >= 16 ? 1 : 16 / ZA;
+    int s = need;
+    while (s % 16 != q) ++s;
+    return s;
+}
+
+// Planes per pass-A/C block: the largest divisor of NZ whose row pairs fit
+// 256 threads in whole warps (per = threads of one plane's RA/2 row pairs).
+__host__ __device__ constexpr int sweep_za(int NZ, int per) {
+    for (int za = per > 0 ? 256 / per : 0; za >= 1; --za)
+        if (NZ % za == 0 && (za * per) % 32 == 0) return za;
+    return 0;
+}
+
+template <int NX, int NY, int NZ>
+struct SweepShape {
+    static constexpr int RA = sweep_ra(NY);
+    static constexpr int RB = RA > 0 ? NY / RA : 1;
+    static constexpr int H = NX / 2 + 1;
+    // pass A and C: row pairs of ZA planes, TFX threads per pair
+    static constexpr int EX = plan_E(NX, false);
+    static constexpr int TFX = NX / EX;
+    static constexpr int ZA = sweep_za(NZ, (RA / 2) * TFX);
+    static constexpr int PA = ZA * RA / 2;
+    static constexpr int NTA = PA * TFX;
+    static constexpr int RP = padded_row(NX);
+    static constexpr int SP = sweep_stage_pitch(RA * H, ZA);
+    static constexpr int XS = (PA * RP > ZA * SP) ? PA * RP : ZA * SP;  // exchange / staging slots
+    static constexpr size_t smem_ac = (size_t)(NX + XS) * sizeof(cpx<float>) + (size_t)PA * 8;
+    // pass B: AG columns a, RB y columns each, TFZ threads per padded column
+    static constexpr int M = 2 * NZ;
+    static constexpr int EZ = plan_E(M, false);
+    static constexpr int TFZ = M / EZ;
+    static constexpr int AG = 256 / (RB * TFZ) > 0 ? 256 / (RB * TFZ) : 1;
+    static constexpr int CB = AG * RB;
+    static constexpr int NTB = CB * TFZ;
+    static constexpr int NGA = (H + AG - 1) / AG;
+    static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
+    static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES +
+                                     (size_t)xchg_slots<float>(M, CB) * sizeof(cpx<float>);
+    static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 && NTA <= 256 &&
+                               NTA % 32 == 0 && NTB <= 256 && RB * TFZ <= 256 && AG * NZ <= NTB &&
+                               TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32;
+};
+
+// Per-box descriptor of a sweep launch (device memory).
+struct SweepBox {
+    const float* rho;       // [NZ][NY][NX]
+    float* phi;             // [NZ][NY][NX]
+    cpx<float>* S;          // half spectrum, [RA][H][RB][NZ]
+    GreenT<float>* green;   // [NY][H] Green's parameters at this solve's time
+    double* tile_sums;      // [NZ][RB] FP64 partial plane sums
+    double* vk0;            // [NZ] FP64 mean-mode potential
+    const double* c00;      // [2NZ - 1] FP64 k = 0 vertical kernel
+    const double* s_dev;    // shear parameter on the device (batched), or null
+    double Lx, Ly, L;       // box lengths and the truncation length L = Lz
+    double scale;           // 4πG / (NX·NY·2NZ)
+    double kzc;             // (π / Lz)²
+    double k0_coef;         // 4πG / (NX·NY)
+};
+
+// Per-launch arguments.  With rho non-null the launch serves one box whose
+// rho, phi and shear parameter s are given here (single solves); otherwise
+// every box takes them from its descriptor.
+struct SweepArgs {
+    const SweepBox* boxes;
+    const float* rho;
+    float* phi;
+    double s;
+    const double* s_dev;    // single box: its shear parameter on the device (a graph replay), or null
+    const cpx<float>* twx;  // e^{-2πi k/NX}, k < NX
+    const cpx<float>* twy;  // e^{-2πi k/NY}, k < NY
+    const cpx<float>* twM;  // e^{-2πi k/2NZ}, k < 2NZ
+    int green_blocks;       // pass A: leading blocks per box that fill the Green's table
+};
+
+// ---------------------------------------------------------------------------
+// pass A
+// ---------------------------------------------------------------------------
+template <int NX, int NY, int NZ>
+__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, NY, NZ>::NTA <= 128 ? 8 : 5))
+    k3_forward(SweepArgs A) {
+    using SH = SweepShape<NX, NY, NZ>;
+    constexpr int RA = SH::RA, RB = SH::RB, H = SH::H, EX = SH::EX, TFX = SH::TFX, ZA = SH::ZA;
+    constexpr int RP = SH::RP, SP = SH::SP, XS = SH::XS;
+    static_assert(SH::ok, "sweep shape");
+    const SweepBox& B = A.boxes[blockIdx.y];
+    if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
+        GreenFill gf;
+        gf.tab = B.green;
+        gf.per_block = (H * NY + A.green_blocks - 1) / A.green_blocks;
+        gf.nx = NX;
+        gf.ny = NY;
+        gf.yhalf = 0;
+        gf.Lx = B.Lx;
+        gf.Ly = B.Ly;
+        gf.L = B.L;
+        gf.s = A.s;
+        gf.s_dev = A.rho != nullptr ? A.s_dev : B.s_dev;
+        green_fill<float>(gf, blockIdx.x);
+        return;
+    }
+    const float* __restrict__ rho = A.rho != nullptr ? A.rho : B.rho;
+    const int bid = (int)blockIdx.x - A.green_blocks;
+    const int zg = bid % (NZ / ZA), j = bid / (NZ / ZA);
+    const int z0 = zg * ZA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* xb = tw + NX;
+    FF* psum = reinterpret_cast<FF*>(xb + XS);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NX; i += SH::NTA) tw[i] = A.twx[i];
+
+    const int t = tid % TFX, c = tid / TFX;
+    const int zl = c / (RA / 2), p = c % (RA / 2);
+    const int z = z0 + zl;
+    const float* r0p = rho + ((size_t)z * NY + j + RB * (2 * p)) * NX;
+    const float* r1p = r0p + (size_t)RB * NX;
+    cpx<float> v[1][EX];
+#pragma unroll
+    for (int e = 0; e < EX; ++e) v[0][e] = {__ldcs(r0p + t + TFX * e), __ldcs(r1p + t + TFX * e)};
+    {
+        // FP64-quality plane sums: compensated float sums of both rows (one
+        // packed pair), double-float reduction over the pair's lanes
+        cpx<float> hi = {0.f, 0.f}, lo = {0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < EX; ++e) {
+            const cpx<float> y = cadd(v[0][e], lo);
+            const cpx<float> tt = cadd(hi, y);
+            lo = csub(y, csub(tt, hi));
+            hi = tt;
+        }
+        FF acc = ff_add(FF{hi.x, lo.x}, FF{hi.y, lo.y});
+#pragma unroll
+        for (int o = TFX / 2; o > 0; o >>= 1) {
+            const FF other = {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+            acc = ff_add(acc, other);
+        }
+        if (t == 0) psum[c] = acc;
+    }
+    __syncthreads();  // twiddles visible
+    const SmemRow<float> buf[1] = {{xb + c * RP, 0}};
+    fft_static<NX, EX, 0, 1, float>(v, t, tw, buf);
+
+    // Hermitian split of the paired transform (Z[n-k] is element E-1-e of lane
+    // TFX-t of the same pair, or of lane 0 itself): X0 = (Z[k] + conj Z[n-k])/2,
+    // X1 = -i (Z[k] - conj Z[n-k])/2, staged as [plane][row][a]
+    __syncthreads();  // the exchange buffer becomes the staging buffer
+    if (tid < ZA) {
+        FF tot = {0.f, 0.f};
+        for (int q = 0; q < RA / 2; ++q) tot = ff_add(tot, psum[tid * (RA / 2) + q]);
+        if (B.tile_sums != nullptr) B.tile_sums[(size_t)(z0 + tid) * RB + j] = (double)tot.hi + (double)tot.lo;
+    }
+    {
+        const int lane = tid & 31;
+        const int src = lane - t + ((TFX - t) & (TFX - 1));
+        cpx<float>* o0 = xb + zl * SP + (2 * p) * H;
+        cpx<float>* o1 = o0 + H;
+        const float half = 0.5f;
+#pragma unroll
+        for (int e = 0; e <= EX / 2; ++e) {
+            const cpx<float> send = v[0][EX - 1 - e];
+            cpx<float> Bz;
+            Bz.x = __shfl_sync(0xffffffffu, send.x, src);
+            Bz.y = __shfl_sync(0xffffffffu, send.y, src);
+            if (t == 0) Bz = v[0][(EX - e) % EX];
+            Bz = cconj(Bz);
+            const cpx<float> Az = v[0][e];
+            if (e < EX / 2 || t == 0) {
+                const int k = t + TFX * e;
+                o0[k] = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
+                o1[k] = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
+            }
+        }
+    }
+    __syncthreads();
+    // y stage 1: for every (z, a) the radix-RA DFT over the rows r
+    cpx<float>* __restrict__ S = B.S;
+    for (int i = tid; i < ZA * H; i += SH::NTA) {
+        const int zi = i % ZA, a = i / ZA;
+        cpx<float> x[RA];
+#pragma unroll
+        for (int r = 0; r < RA; ++r) x[r] = xb[zi * SP + r * H + a];
+        Dft<RA, float>::run(x);
+        cpx<float>* dst = S + ((size_t)a * RB + j) * NZ + z0 + zi;
+#pragma unroll
+        for (int k = 0; k < RA; ++k) dst[(size_t)k * H * RB * NZ] = x[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass B
+// ---------------------------------------------------------------------------
+template <int NX, int NY, int NZ>
+__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, NY, NZ>::EZ > 16 ? 3 : 4))
+    k3_middle(SweepArgs A) {
+    using SH = SweepShape<NX, NY, NZ>;
+    constexpr int RA = SH::RA, RB = SH::RB, H = SH::H, M = SH::M, EZ = SH::EZ, TFZ = SH::TFZ;
+    constexpr int AG = SH::AG, CB = SH::CB, NGA = SH::NGA;
+    static_assert(SH::ok, "sweep shape");
+    const SweepBox& B = A.boxes[blockIdx.y];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* twM = reinterpret_cast<cpx<float>*>(smem_raw);
+    GreenT<float>* gm = reinterpret_cast<GreenT<float>*>(twM + M);
+    cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
+    const int tid = threadIdx.x;
+    if ((int)blockIdx.x == RA * NGA) {
+        // the FP64 mean mode: vk0[i] = coef Σ_j c00[i - j + NZ - 1] S[j] from the plane sums
+        if (B.vk0 != nullptr) {
+            ZArgs za;
+            za.tile_sums = B.tile_sums;
+            za.tiles_per_plane = RB;
+            za.c00 = B.c00;
+            za.k0_coef = B.k0_coef;
+            za.vk0 = B.vk0;
+            mean_mode_fp64(za, NZ, reinterpret_cast<double*>(xb));
+        }
+        return;
+    }
+    const int k = (int)blockIdx.x / NGA, ag = (int)blockIdx.x % NGA;
+    const int a0 = ag * AG;
+    for (int i = tid; i < M; i += SH::NTB) twM[i] = A.twM[i];
+    if (tid < CB) {
+        const int a = a0 + tid / RB, b = k + RA * (tid % RB);
+        GreenT<float> g = {};
+        g.kzero = 1;  // columns past the half spectrum: finite, never stored
+        g.same = 1;
+        if (a < H) g = B.green[(size_t)b * H + a];
+        gm[tid] = g;
+    }
+    cpx<float>* __restrict__ S = B.S;
+    const size_t tile = ((size_t)k * H + a0) * RB * NZ;  // this block's [AG][RB][NZ] tile
+    // y stage 2 (forward): item (al, z) takes twiddle ω_NY^{k·j} and the
+    // radix-RB DFT over j; output r' is column al·RB + r' (b = k + RA·r')
+    const int zi = tid % NZ, al = tid / NZ;
+    const bool item = tid < AG * NZ && a0 + al < H;
+    if (item) {
+        cpx<float> x[RB];
+        const cpx<float>* src = S + tile + (size_t)al * RB * NZ + zi;
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) x[jj] = src[(size_t)jj * NZ];
+#pragma unroll
+        for (int jj = 1; jj < RB; ++jj) x[jj] = cmul(x[jj], A.twy[(k * jj) % NY]);
+        Dft<RB, float>::run(x);
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
+            col[zi] = x[rr];
+        }
+    } else if (tid < AG * NZ) {
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
+            col[zi] = {0.f, 0.f};
+        }
+    }
+    __syncthreads();
+
+    // padded z transform per column (as k_z_padded)
+    const int c = tid % CB, t = tid / CB;
+    const XchgCol<float, CB> buf[1] = {{xb + c, 0}};
+    cpx<float> v[1][EZ];
+#pragma unroll
+    for (int e = 0; e < EZ / 2; ++e) v[0][e] = buf[0][t + TFZ * e];
+    fft_static_padded<M, EZ, 1, float>(v, t, twM, buf);  // starts with a barrier
+    {
+        const float scale = (float)B.scale;
+        const GreenCoef<float> q = green_coef<float>(gm[c], scale, true);
+        const float kzc = (float)B.kzc;
+        const float L2half = (float)(0.5 * B.L * B.L);
+        static_assert(TFZ % 2 == 0 && (CB * TFZ) % 32 == 0, "padded z shape");
+        if (__all_sync(0xffffffffu, q.same && !q.kzero)) {
+            const float num = (t & 1) ? q.ao : q.ae;
+            const float tf = (float)t;
+#pragma unroll
+            for (int e = 0; e < EZ; ++e) {
+                const float ms = (e < EZ / 2) ? tf + (float)(TFZ * e) : (float)(M - TFZ * e) - tf;
+                const float f = fast_div(num, fmaf(kzc * ms, ms, q.k2a));
+                v[0][e] = cconj_scale(v[0][e], f);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < EZ; ++e) {
+                const int m = t + TFZ * e;
+                const int ms = (m <= NZ) ? m : M - m;
+                const float f = green_factor<float>(q, m, ms, kzc, scale, L2half);
+                v[0][e] = {v[0][e].x * f, -v[0][e].y * f};
+            }
+        }
+    }
+    fft_static<M, EZ, 0, 1, float>(v, t, twM, buf);
+    // v[e] (e < EZ/2) is the conjugate of the convolved column at z = t + TFZ·e:
+    // exactly the input the inverse y transform's first stage wants
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < EZ / 2; ++e) buf[0][t + TFZ * e] = v[0][e];
+    __syncthreads();
+    if (item) {
+        cpx<float> x[RB];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) {
+            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
+            x[rr] = col[zi];
+        }
+        Dft<RB, float>::run(x);
+        cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
+#pragma unroll
+        for (int kp = 0; kp < RB; ++kp) dst[(size_t)kp * NZ] = x[kp];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass C
+// ---------------------------------------------------------------------------
+template <int NX, int NY, int NZ>
+__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, NY, NZ>::NTA <= 128 ? 8 : 4))
+    k3_inverse(SweepArgs A) {
+    using SH = SweepShape<NX, NY, NZ>;
+    constexpr int RA = SH::RA, RB = SH::RB, H = SH::H, EX = SH::EX, TFX = SH::TFX, ZA = SH::ZA;
+    constexpr int RP = SH::RP, SP = SH::SP;
+    static_assert(SH::ok, "sweep shape");
+    const SweepBox& B = A.boxes[blockIdx.y];
+    float* __restrict__ phi = A.rho != nullptr ? A.phi : B.phi;
+    const int bid = blockIdx.x;
+    const int zg = bid % (NZ / ZA), j = bid / (NZ / ZA);
+    const int z0 = zg * ZA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
+    cpx<float>* xb = tw + NX;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < NX; i += SH::NTA) tw[i] = A.twx[i];
+    // y stage 2 of the inverse: twiddle ω_NY^{j·k} and the radix-RA DFT over k
+    // give rows j + RB·r of the conjugated inverse y transform
+    const cpx<float>* __restrict__ S = B.S;
+    for (int i = tid; i < ZA * H; i += SH::NTA) {
+        const int zi = i % ZA, a = i / ZA;
+        cpx<float> x[RA];
+        const cpx<float>* src = S + ((size_t)a * RB + j) * NZ + z0 + zi;
+#pragma unroll
+        for (int k = 0; k < RA; ++k) x[k] = src[(size_t)k * H * RB * NZ];
+#pragma unroll
+        for (int k = 1; k < RA; ++k) x[k] = cmul(x[k], A.twy[(j * k) % NY]);
+        Dft<RA, float>::run(x);
+#pragma unroll
+        for (int r = 0; r < RA; ++r) xb[zi * SP + r * H + a] = x[r];
+    }
+    __syncthreads();
+
+    // x inverse of the row pair (2p, 2p+1) of plane zl.  The staging holds
+    // c0 = conj X0 and c1 = conj X1; the transform input is conj Z with
+    // Z[k] = X0[k] + i X1[k] (k ≤ n/2) or conj X0[n-k] + i conj X1[n-k].
+    const int t = tid % TFX, c = tid / TFX;
+    const int zl = c / (RA / 2), p = c % (RA / 2);
+    const int z = z0 + zl;
+    const cpx<float>* w0 = xb + zl * SP + (2 * p) * H;
+    const cpx<float>* w1 = w0 + H;
+    cpx<float> v[1][EX];
+#pragma unroll
+    for (int e = 0; e < EX; ++e) {
+        const int k = t + TFX * e;
+        if (2 * k <= NX) {
+            cpx<float> c0 = w0[k], c1 = w1[k];
+            if (k == 0 || 2 * k == NX) {
+                c0.y = 0.f;
+                c1.y = 0.f;
+            }
+            v[0][e] = {c0.x + c1.y, c0.y - c1.x};
+        } else {
+            const cpx<float> c0 = w0[NX - k], c1 = w1[NX - k];
+            v[0][e] = {c0.x - c1.y, -c0.y - c1.x};
+        }
+    }
+    const SmemRow<float> buf[1] = {{xb + c * RP, 0}};
+    fft_static<NX, EX, 0, 1, float>(v, t, tw, buf);  // its first exchange follows a barrier
+    float add_hi = 0.f, add_lo = 0.f;
+    if (B.vk0 != nullptr) {
+        const double vv = B.vk0[z];
+        add_hi = (float)vv;
+        add_lo = (float)(vv - (double)add_hi);
+    }
+    float* o0 = phi + ((size_t)z * NY + j + RB * (2 * p)) * NX;
+    float* o1 = o0 + (size_t)RB * NX;
+#pragma unroll
+    for (int e = 0; e < EX; ++e) {
+        const int x = t + TFX * e;
+        // conj of the forward result, plus the FP64 mean mode as a TwoSum of
+        // (p0, p1) + hi, then + lo, on both rows at once as packed pairs
+        const cpx<float> a = {v[0][e].x, -v[0][e].y}, hh = {add_hi, add_hi}, ll = {add_lo, add_lo};
+        const cpx<float> sm = cadd(a, hh);
+        const cpx<float> bb = csub(sm, a);
+        const cpx<float> er = cadd(csub(a, csub(sm, bb)), csub(hh, bb));
+        const cpx<float> r = cadd(sm, cadd(er, ll));
+        __stcs(o0 + x, r.x);
+        __stcs(o1 + x, r.y);
+    }
+}
+
+}  // namespace sbp

@@ -28,11 +28,14 @@ def main(argv=None):
     ap.add_argument("--frame", type=int, default=0, help="1: physical frame (Sect. 2.1 mapping)")
     ap.add_argument("--method", type=int, default=0, help="1, 2: SASHA (Sect. 2.2)")
     ap.add_argument("--force", action="store_true", help="also take -grad(phi) after each solve")
+    ap.add_argument("--schedule", type=int, default=0, help="1: five passes, 2: three sweeps (0: automatic)")
     args = ap.parse_args(argv)
     nx, ny, nz = (int(v) for v in args.box.lower().split("x"))
     Lx, Ly, Lz = (float(v) for v in args.lengths.split(","))
     dt = sbp.DType.F32 if args.dtype == "f32" else sbp.DType.F64
     plan = sbp.Plan(nx, ny, nz, Lx, Ly, Lz, dtype=dt)
+    if args.schedule:
+        plan.set_option(sbp.Option.SCHEDULE, args.schedule)
     if args.z_variant:
         plan.set_option(sbp.Option.Z_VARIANT, args.z_variant)
     if args.xy_passes:

@@ -42,6 +42,9 @@ class Stage(IntEnum):
     X_INVERSE = 4
     GREEN_TABLE = 5
     GREEN_FILL = 6
+    SWEEP_FORWARD = 7
+    SWEEP_MIDDLE = 8
+    SWEEP_INVERSE = 9
 
 
 class Option(IntEnum):
@@ -54,6 +57,7 @@ class Option(IntEnum):
     FRAME = 7
     METHOD = 8
     XY_CHUNK = 9
+    SCHEDULE = 10
 
 
 class SbpError(RuntimeError):
@@ -89,6 +93,7 @@ SIGNATURES = {
     "sbp_version": (ctypes.c_char_p, []),
     "sbp_solve_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
                                    _c_double, _vp, _vp, _c_double, _vp]),
+    "sbp_plan_query": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_double)]),
 }
 
 _lib = None
@@ -171,6 +176,16 @@ class Plan:
                                float(t), _stream_handle(stream)), "sbp_solve")
         return phi
 
+    def query(self, what: int) -> float:
+        """sbp_plan_query: 1 = the schedule solves run (1 five passes, 2 three
+        sweeps), 2 = kernels per sbp_solve."""
+        v = ctypes.c_double()
+        _check(lib().sbp_plan_query(self._h, int(what), ctypes.byref(v)), "sbp_plan_query")
+        return v.value
+
+    def schedule_is_sweep(self) -> bool:
+        return self.query(1) == 2.0
+
     def set_option(self, option, value):
         _check(lib().sbp_plan_set_option(self._h, int(option), float(value)), "sbp_plan_set_option")
 
@@ -207,8 +222,9 @@ class Plan:
 
     def run_stage(self, stage, inp, out, t: float = 0.0, stream=None):
         ip = ctypes.c_void_p(inp.data_ptr()) if inp is not None else None
-        _check(lib().sbp_run_stage(self._h, int(stage), ip, ctypes.c_void_p(out.data_ptr()), float(t),
-                                   _stream_handle(stream)), f"sbp_run_stage({Stage(stage).name})")
+        op = ctypes.c_void_p(out.data_ptr()) if out is not None else None
+        _check(lib().sbp_run_stage(self._h, int(stage), ip, op, float(t), _stream_handle(stream)),
+               f"sbp_run_stage({Stage(stage).name})")
         return out
 
     def close(self):
@@ -237,6 +253,11 @@ def solve_batched(plans, rhos, phis, ts, stream=None):
     tp = (ctypes.c_double * n)(*[float(t) for t in ts])
     _check(lib().sbp_solve_batched(n, hp, rp, fp, tp, _stream_handle(stream)), "sbp_solve_batched")
     return phis
+
+
+def batched_launches(plans) -> int:
+    """Kernels one sbp_solve_batched call over these plans launches."""
+    return int(sum(p.query(2) for p in plans))
 
 
 def solve_noalloc(rho, phi, Lx, Ly, Lz, q=1.5, Omega=1.0, G=1.0, t=0.0, stream=None):

@@ -12,6 +12,31 @@ def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
+def plane_mean_removed(a):
+    """Φ minus its mean over every z-plane: the k ≠ 0 part of the solution."""
+    a = np.asarray(a, dtype=np.float64)
+    return a - a.mean(axis=(-2, -1), keepdims=True)
+
+
+def max_rel(a, b):
+    """max |a - b| relative to max |b|."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def parity(got, want, tol):
+    """The three end-to-end bars: rel-L2 of Φ, rel-L2 of Φ without its plane
+    means (the k = 0 mode dominates ‖Φ‖ for stratified densities and would hide
+    errors in the rest), and the max-norm error relative to ‖Φ‖∞.  Returns
+    the three errors; asserts each ≤ tol."""
+    e1 = rel_l2(got, want)
+    e2 = rel_l2(plane_mean_removed(got), plane_mean_removed(want))
+    e3 = max_rel(got, want)
+    assert e1 <= tol and e2 <= tol and e3 <= tol, (e1, e2, e3, tol)
+    return e1, e2, e3
+
+
 def torch_dtype(dtype):
     import torch
 
