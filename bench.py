@@ -261,7 +261,9 @@ def _oracle_job(spec):
     from paper_2510_10070_gb300 import workloads as W
 
     b = W.Box(*spec["box"])
-    if spec["kind"] == "noisy":
+    if spec["kind"] == "array":  # the density itself, built by the caller
+        rho = np.asarray(spec["rho"], dtype=np.float64)
+    elif spec["kind"] == "noisy":
         rho = W.noisy_gaussian(b, seed=spec["seed"])
     else:
         rho = W.lognormal_disc(b, seed=spec["seed"], sigma=spec["sigma"])
@@ -291,10 +293,12 @@ class OraclePool:
         self.pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
 
     def run(self, specs):
-        """Run the specs concurrently; (wall s for all, [(wall, cpu, phi)])."""
-        t0 = time.perf_counter()
+        """Run the specs concurrently, one per process; returns (the longest
+        solve, [(wall, cpu, phi)]).  Each process builds its input before its
+        clock starts, so the longest solve is the time in which every core
+        solved one box."""
         out = self.pool.map(_oracle_job, specs, chunksize=1)
-        return time.perf_counter() - t0, out
+        return max(o[0] for o in out), out
 
     def close(self):
         self.pool.close()
@@ -340,7 +344,7 @@ def cpu_batch_baseline(pool, boxes, extra_256=None):
         wall, out = pool.run(jobs)
         rates[shape] = cores / wall
         cpu = sum(o[1] for o in out)
-        details["x".join(map(str, shape))] = {"boxes": cores, "wall_s": wall, "solves_per_s": cores / wall,
+        details["x".join(map(str, shape))] = {"boxes": cores, "longest_solve_s": wall, "solves_per_s": cores / wall,
                                               "mean_box_s": statistics.mean(o[0] for o in out),
                                               "cores_busy": cpu / wall}
         if extra_256 is not None and shape == (256, 256, 128):
@@ -517,7 +521,7 @@ def main():
     value = job_rate(nbox, args.steps, world, ms)
     cells = sum(b.cells for b in boxes)
     balg = sum(alg_bytes(b, rb) for b in boxes)
-    kernels_per_solve = [3 if (p.dtype == sbp.DType.F32 and p.schedule_is_sweep()) else 5 for p in plans]
+    launches_per_step, grouped_boxes = sbp.batch_info(plans, rhos, phis)
 
     # End to end: every step copies its inputs from pinned host memory, solves
     # through sbp_solve_batched and copies its results back.  All boxes sit in
@@ -615,32 +619,43 @@ def main():
                     "note": "FP32 batch output of the timed step; the FP64 GPU solves are pinned to the FP64 "
                             "oracle at <= 1e-12 rel-L2 by the test suite"}
 
-    # ---- dominant kernel: the middle pass of the largest box (the z pass on
-    # the five-pass schedule), timed alone with CUDA events on the launching
-    # stream, L2 overwritten before every launch
+    # ---- dominant kernel: the middle sweep of the largest shape, launched for
+    # all boxes of that shape at once as the batch graph runs it (the padded z
+    # pass of one box where that shape runs five passes), timed alone with
+    # CUDA events on the launching stream, L2 overwritten before every launch
     big = max(range(nbox), key=lambda i: boxes[i].cells)
     bp, bb = plans[big], boxes[big]
+    big_shape = shape_of(bb)
+    nbig = sum(1 for b in boxes if shape_of(b) == big_shape)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    if bp.schedule_is_sweep():
-        bp.run_stage(sbp.Stage.SWEEP_FORWARD, rhos[big], None, t=times[big], stream=stream)
+    grouped_dominant = False
+    if args.workload == "batch96":
+        try:
+            sbp.batch_run_stage(plans, rhos, phis, big_shape, sbp.Stage.SWEEP_MIDDLE, stream=stream)
+            grouped_dominant = True
+        except sbp.SbpError:
+            grouped_dominant = False
+    if grouped_dominant:
         zname = f"k3_middle<{bb.nx}, {bb.ny}, {bb.nz}>"
-        what = "middle sweep: second y stage, padded z pass with the Green's multiply, first inverse y stage"
+        what = (f"middle sweep: second y stage, padded z pass with the Green's multiply, first inverse y stage; "
+                f"one launch for the {nbig} boxes of this shape, as in the batch graph")
+        zbytes = nbig * middle_pass_bytes(bb, rb)
 
         def launch():
-            bp.run_stage(sbp.Stage.SWEEP_MIDDLE, None, None, t=times[big], stream=stream)
+            sbp.batch_run_stage(plans, rhos, phis, big_shape, sbp.Stage.SWEEP_MIDDLE, stream=stream)
     else:
         spec = bp.new_spectrum()
         bp.run_stage(sbp.Stage.X_FORWARD, rhos[big], spec, stream=stream)
         bp.run_stage(sbp.Stage.Y_FORWARD, spec, spec, stream=stream)
         bp.run_stage(sbp.Stage.GREEN_FILL, None, spec, t=times[big], stream=stream)
         zname = f"k_z_padded<{'float' if dt == 1 else 'double'}, {16 if dt == 1 else 8}, {bb.nz}>"
-        what = "padded z pass"
+        what = "padded z pass of one box"
+        zbytes = middle_pass_bytes(bb, rb)
 
         def launch():
             bp.run_stage(sbp.Stage.Z_CONVOLVE, spec, spec, stream=stream)
     z_ms = event_time_ms(launch, stream, 20, flush=flush)
     z_ms_warm = event_time_ms(launch, stream, 20)
-    zbytes = middle_pass_bytes(bb, rb)
     z_gbs = zbytes / (z_ms / 1e3) / 1e9
     traffic, rec = recorded_traffic(zname)
     roofline = {"bound": "hbm", "kernel": f"{zname} ({what}), {bb.nx}x{bb.ny}x{bb.nz}",
@@ -734,7 +749,8 @@ def main():
                                        "fp32_vs_fp64_gpu": errors(o32, o64)}
         g = torch.empty((3,) + tuple(rho2.shape), dtype=torch.float32, device=dev)
         phi2 = out2[1.3][1]
-        mf = event_time_ms(lambda: p32.force(phi2, t=1.3, out=g, stream=stream), stream, 20, flush=flush)
+        pf = plan_for(b2, 1)
+        mf = event_time_ms(lambda: pf.force(phi2, t=1.3, out=g, stream=stream), stream, 20, flush=flush)
         side["config2_force_fp32"] = {"ms_per_call": mf,
                                       "gb_per_s": 4 * phi2.numel() * 4 / (mf / 1e3) / 1e9}
         side["batch_fp32_vs_config2_fp64_cells_speedup"] = (cells / (ms_per_step / 1e3) / 1e9) / \
@@ -748,8 +764,7 @@ def main():
             cores = pool.cores
             b1 = W.BOX_32
             cfg1 = {"kind": "noisy", "box": box_tuple(b1), "seed": 0, "t": W.T_32}
-            cfg3 = {"kind": "lognormal", "box": box_tuple(b3), "seed": 3, "sigma": 0.5, "t": W.T_512,
-                    "down": (8, 8, 4), "f32": True}
+            cfg3 = {"kind": "array", "rho": small, "box": box_tuple(sb), "t": W.T_512}
             for name, spec, box in (("config1_32x32x32", cfg1, b1), ("config3_copy_64x64x64", cfg3, sb)):
                 one = _run_single(spec)
                 wall, _ = pool.run([spec] * cores)
@@ -765,8 +780,9 @@ def main():
         cores = pool.cores
         cpu = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
                "sample": f"one round per size class of the batch: {cores} spawned processes (one per host core, "
-                         f"one BLAS thread each) each solved one box of that class with the FP64 oracle; batch "
-                         f"rate = {nbox} / sum over classes of count / class rate",
+                         f"one BLAS thread each) each solved one box of that class with the FP64 oracle at the same "
+                         f"time; class rate = {cores} / the round's longest solve; batch rate = {nbox} / sum over "
+                         f"classes of count / class rate",
                "classes": details}
         if kept is not None:
             wall, cpu_s, phi_o = kept
@@ -788,13 +804,14 @@ def main():
                   "alg_bytes_per_step": balg, "l2": "inputs larger than L2 (no flush needed)"
                   if sum(r.numel() * r.element_size() for r in rhos) > 129e6 else "inputs smaller than L2",
                   "parallelism": f"replicas x{world}",
-                  "schedule": {"three_sweeps": sum(k == 3 for k in kernels_per_solve),
-                               "five_passes": sum(k == 5 for k in kernels_per_solve)}}
+                  "schedule": {"boxes_in_grouped_sweeps": grouped_boxes,
+                               "boxes_on_own_kernels": nbox - grouped_boxes,
+                               "kernel_launches_per_step": launches_per_step}}
         line = result_line(args, world, value, ms_per_step, "f64" if dt == 0 else "f32", config,
                            roofline=roofline, cpu_baseline=cpu,
                            e2e={"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                                 "d2h_bytes_per_step": h2d},
-                           gpu_launches=sbp.batched_launches(plans) * args.steps,
+                           gpu_launches=launches_per_step * args.steps,
                            clocks=clk.summary(), accuracy=accuracy, single_box=side)
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -110,26 +110,41 @@ sbp_status sbp_solve(sbp_plan p, const void* rho, void* phi, double t, void* str
 /*
  * sbp_solve_batched — nbox independent solves on one stream.
  *
- * Each box i is solved exactly as sbp_solve(plans[i], rho[i], phi[i], t[i])
- * (bit for bit).  All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE)
+ * Each box i is solved as sbp_solve(plans[i], rho[i], phi[i], t[i]) (bit for
+ * bit when both run the same schedule, see below).  All plans must share a dtype (else SBP_ERR_NOT_SAME_DTYPE)
  * and the device.  A plan may appear only once per call.  plans, rho, phi and
  * t are HOST arrays of length nbox; rho[i] and phi[i] are device pointers.
  * phi[i] == rho[i] (in place) is allowed, as in sbp_solve.  The boxes run
  * concurrently, so a box's phi must not overlap another box's rho or phi
  * (SBP_ERR_INVALID_ARG); boxes may share the same rho.
  *
- * Execution: the boxes' pass kernels are captured once into a CUDA graph with
- * K parallel branches and cached by the exact (plans, rho, phi) tuple; a call
+ * Execution: boxes whose plans run the three sweeps (SBP_OPT_SCHEDULE) are
+ * grouped by shape, and one launch per sweep covers all boxes of a group
+ * through a device table of per-box descriptors; the other boxes keep their
+ * own pass kernels, spread over K parallel branches.  All of it is captured
+ * once into a CUDA graph, cached by the exact (plans, rho, phi) tuple; a call
  * with a cached tuple copies the nbox shear parameters to the device and
- * replays the graph on `stream`.  The first call of a tuple chooses K (and
- * whether the x/y passes run in L2-sized chunks) by timing candidate graphs
- * on `stream` (it synchronises that stream once); the candidates write into
- * temporary outputs that the call allocates and frees, so the caller's
- * buffers see exactly one solve per call; a later tuple with the same
- * plans and other buffers (double buffering) takes that choice without
- * timing.  The environment variables SBP_BATCH_BRANCHES=K and
- * SBP_BATCH_CHUNK=0/1 force the choice.  Destroying or reconfiguring any
- * plan of a tuple drops its cached graph.
+ * replays the graph on `stream`.  The first call of a tuple tunes by timing
+ * candidate graphs on `stream` (it synchronises that stream): each group as
+ * grouped sweeps and as per-box five-pass kernels (the faster is kept; the
+ * grouped sweeps unless they are more than 2% slower), then K (and whether
+ * five-pass x/y passes run in L2-sized chunks) on the whole graph, then each
+ * group's schedule flipped in turn on the whole graph (kept if the batch is
+ * more than 1% faster: groups share the SMs).  The
+ * candidates write into temporary outputs that the call allocates and
+ * frees, so the caller's buffers see exactly one solve per call.  The choice
+ * is remembered for the same plans' shapes on the same GPU type, in the
+ * process and, when the environment variable SBP_TUNE_CACHE names a file, in
+ * that file (one line per choice, appended), so later processes skip the
+ * timing.  A later tuple with the same plans and other buffers (double
+ * buffering) takes the choice without timing.  The environment variables
+ * SBP_BATCH_BRANCHES=K, SBP_BATCH_CHUNK=0/1 and SBP_BATCH_SCHEDULE=1/2 (five
+ * passes / grouped sweeps) force the choice; SBP_TUNE_LOG=1 prints the
+ * timings and the choice to stderr.  Destroying or reconfiguring any
+ * plan of a tuple drops its cached graph.  With grouped boxes the result may
+ * differ from sbp_solve's by rounding where a group chose the five passes
+ * while sbp_solve of that plan runs the sweeps, or the reverse; each box still
+ * meets the solver's accuracy.
  */
 sbp_status sbp_solve_batched(int nbox, const sbp_plan* plans, const void* const* rho,
                              void* const* phi, const double* t, void* stream);
@@ -361,6 +376,29 @@ sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, doubl
 sbp_status sbp_solve_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz,
                              double q, double Omega, double G,
                              const float* rho, float* phi, double t, void* stream);
+
+/* sbp_batch_info — what one sbp_solve_batched call over exactly these
+ * (plans, rho, phi) launches, once its graph exists (after the first call):
+ * *launches = kernels per call, *grouped_boxes = boxes solved by grouped
+ * three-sweep launches (one launch per sweep for all boxes of a shape).
+ * Either output may be NULL.  SBP_ERR_INVALID_ARG if no graph is cached for
+ * the tuple.  Not part of the paper's method: a report of the schedule. */
+sbp_status sbp_batch_info(int nbox, const sbp_plan* plans, const void* const* rho, void* const* phi,
+                          int* launches, int* grouped_boxes);
+
+/* sbp_batch_run_stage — one sweep of one group of a cached batch, alone (for
+ * stage-level tests and for timing a grouped launch as the batch runs it).
+ * The tuple (plans, rho, phi) must have a graph from an earlier
+ * sbp_solve_batched call; (nx, ny, nz) picks the group of boxes of that
+ * shape that runs grouped sweeps; stage is SBP_STAGE_SWEEP_FORWARD, _MIDDLE
+ * or _INVERSE.  The launch covers every box of the group with the shear
+ * times of the last sbp_solve_batched call, reading and writing the plans'
+ * workspaces and the tuple's rho (forward) or phi (inverse) like the graph
+ * does.  Run in order, the three stages give the batched result of those
+ * boxes.  SBP_ERR_INVALID_ARG if no such graph or group.  Not part of the
+ * paper's method. */
+sbp_status sbp_batch_run_stage(int nbox, const sbp_plan* plans, const void* const* rho, void* const* phi,
+                               int nx, int ny, int nz, int stage, void* stream);
 
 /* sbp_plan_query — what a plan's solves do now (not part of the paper's
  * method; for callers that report or schedule work).  what:

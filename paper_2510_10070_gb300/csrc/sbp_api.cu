@@ -8,8 +8,10 @@
 #include <cstdint>
 #include <cstring>
 #include <cstdlib>
+#include <cstdio>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/sbp.h"
@@ -1095,10 +1097,11 @@ sbp_status solve_sweep(const sbp_plan_s* p, const void* rho, void* phi, double t
     return launch_sweep(p, a, 1, st);
 }
 
-// Kernels one solve launches (solve_t's dispatch; chunk < 0: the plan's own).
-int launches_per_solve(const sbp_plan_s* p, int chunk) {
+// Kernels one solve launches (solve_t's dispatch; chunk < 0: the plan's own;
+// five: the five-pass kernels even where the plan runs the sweeps).
+int launches_per_solve(const sbp_plan_s* p, int chunk, bool five = false) {
     if (chunk < 0) chunk = p->chunk;
-    if (p->sweep && chunk <= 0) return 3;
+    if (p->sweep && !five && chunk <= 0) return 3;
     const int sasha = p->method != 0 ? 1 : 0;
     if (p->frame) return 5 + sasha;
     if (p->xy_fused) return 3;
@@ -1106,10 +1109,14 @@ int launches_per_solve(const sbp_plan_s* p, int chunk) {
     return 5 + sasha;
 }
 
+// chunk: planes per x/y chunk (-1: the plan's own setting; -2: the five-pass
+// kernels without chunks even where the plan runs the sweeps).
 template <typename T>
 sbp_status solve_t(sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
                    const double* s_dev = nullptr, int chunk = -1) {
-    if (p->sweep && chunk <= 0) return solve_sweep(p, rho, phi, t, st, s_dev);
+    const bool five = (chunk == -2);
+    if (five) chunk = 0;
+    if (p->sweep && !five && chunk <= 0) return solve_sweep(p, rho, phi, t, st, s_dev);
     if (p->frame) return solve_physical_t<T>(p, rho, phi, t, st, s_dev);
     if (p->xy_fused) return solve_fused_t<T>(p, rho, phi, t, st, s_dev);
     if (chunk < 0) chunk = p->chunk;
@@ -1155,23 +1162,39 @@ sbp_status check_io(const sbp_plan_s* p, const void* rho, const void* phi, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Batched executor: the boxes' pass kernels captured once into a CUDA graph
-// with K parallel branches (boxes spread over the branches, largest first),
-// cached by the exact (plans, rho, phi) tuple.  Per call only the shear
-// parameters change: one async copy refreshes a device table that the
-// x-forward Green's blocks read, then the graph is replayed.  K is chosen on
-// the first call by timing the candidates (SBP_BATCH_BRANCHES forces it).
+// Batched executor.  Boxes whose plans run the three-sweep kernels are grouped
+// by shape: one launch per sweep covers every box of the group through a
+// device table of per-box descriptors (pointers, shear parameter, physical
+// constants).  The other boxes keep their own pass kernels, spread over K
+// parallel branches (largest first).  Everything is captured once into a
+// CUDA graph, cached by the exact (plans, rho, phi) tuple; a call copies the
+// boxes' shear parameters to the device and replays the graph.
+//
+// The first call of a tuple tunes: each group is timed as grouped sweeps and
+// as per-box five-pass kernels and keeps the faster; then the branch count K
+// (and chunked x/y passes for five-pass boxes) is timed on the whole graph.
+// The candidates write into temporary outputs.  The choice is remembered per
+// batch shape and GPU (and in the file named by SBP_TUNE_CACHE, if set).
 // ---------------------------------------------------------------------------
+struct SweepGroup {
+    std::vector<int> boxes;  // box indices of the call, in table order
+    int first = 0;           // first descriptor of the group in the table
+    bool use = true;         // grouped sweeps (else per-box five-pass kernels)
+};
+
 struct BatchExec {
     std::vector<sbp_plan_s*> plans;
     std::vector<const void*> rho;
     std::vector<void*> phi;
     int device = 0;
     double* s_dev = nullptr;
+    SweepBox* table = nullptr;           // device descriptors of the grouped boxes
+    std::vector<SweepGroup> groups;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int branches = 0;
-    int chunked = 0;  // the boxes' x/y passes run in chunks (auto_chunk)
+    int chunked = 0;  // the five-pass boxes' x/y passes run in chunks (auto_chunk)
+    int launches = 0;  // kernels one replay launches
     float tuned_ms = 0.f;
 };
 
@@ -1183,6 +1206,7 @@ void free_exec(BatchExec* e) {
     if (e->exec) cudaGraphExecDestroy(e->exec);
     if (e->graph) cudaGraphDestroy(e->graph);
     if (e->s_dev) cudaFree(e->s_dev);
+    if (e->table) cudaFree(e->table);
     delete e;
 }
 
@@ -1211,43 +1235,139 @@ int auto_chunk(const sbp_plan_s* p) {
     return c >= p->nz ? 0 : c;
 }
 
-sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out) {
+// Groups of sweep boxes (same shape) and their descriptor table.  `phi` are
+// the outputs the descriptors point to.
+sbp_status build_groups(BatchExec* e, const std::vector<void*>& phi, cudaStream_t st) {
     const int n = (int)e->plans.size();
+    if (e->groups.empty()) {
+        for (int i = 0; i < n; ++i) {
+            const sbp_plan_s* p = e->plans[i];
+            if (!p->sweep) continue;
+            SweepGroup* g = nullptr;
+            for (SweepGroup& c : e->groups) {
+                const sbp_plan_s* q = e->plans[c.boxes[0]];
+                if (q->nx == p->nx && q->ny == p->ny && q->nz == p->nz) g = &c;
+            }
+            if (!g) {
+                e->groups.emplace_back();
+                g = &e->groups.back();
+            }
+            g->boxes.push_back(i);
+        }
+        int first = 0;
+        for (SweepGroup& g : e->groups) {
+            g.first = first;
+            first += (int)g.boxes.size();
+        }
+        if (first > 0 && cudaMalloc(&e->table, sizeof(SweepBox) * first) != cudaSuccess) {
+            cudaGetLastError();
+            e->table = nullptr;
+            return SBP_ERR_OUT_OF_MEMORY;
+        }
+    }
+    std::vector<SweepBox> host;
+    for (const SweepGroup& g : e->groups) {
+        for (int i : g.boxes) {
+            const sbp_plan_s* p = e->plans[i];
+            SweepBox d;
+            std::memset(&d, 0, sizeof(d));
+            d.rho = static_cast<const float*>(e->rho[i]);
+            d.phi = static_cast<float*>(phi[i]);
+            d.S = reinterpret_cast<cpx<float>*>(p->W);
+            d.green = reinterpret_cast<GreenT<float>*>(p->green);
+            d.tile_sums = p->tile_sums;
+            d.vk0 = p->vk0;
+            d.c00 = p->c00;
+            d.s_dev = e->s_dev + i;
+            d.Lx = p->Lx;
+            d.Ly = p->Ly;
+            d.L = p->alpha * p->Lz;
+            d.scale = 4.0 * M_PI * p->G / ((double)p->nx * p->ny * 2.0 * p->nz);
+            d.kzc = (M_PI / p->Lz) * (M_PI / p->Lz);
+            d.k0_coef = 4.0 * M_PI * p->G / ((double)p->nx * p->ny);
+            host.push_back(d);
+        }
+    }
+    if (!host.empty() && cudaMemcpyAsync(e->table, host.data(), sizeof(SweepBox) * host.size(),
+                                         cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    // pageable source: the copy is staged before cudaMemcpyAsync returns
+    return SBP_OK;
+}
+
+// Which boxes a capture covers: all (mask empty) or those with mask[i] != 0.
+sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_out, cudaGraphExec_t* exec_out,
+                         int* launches_out, const std::vector<char>& mask = {}) {
+    const int n = (int)e->plans.size();
+    auto in = [&](int i) { return mask.empty() || mask[i] != 0; };
+    std::vector<char> grouped(n, 0);
+    int ngroups = 0;
+    for (const SweepGroup& g : e->groups) {
+        if (!g.use) continue;
+        bool any = false;
+        for (int i : g.boxes) {
+            grouped[i] = 1;
+            any = any || in(i);
+        }
+        if (any) ++ngroups;
+    }
+    const int nb = K + ngroups;
     cudaStream_t cap = nullptr;
-    std::vector<cudaStream_t> br(K, nullptr);
+    std::vector<cudaStream_t> br(nb, nullptr);
     cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> join(K, nullptr);
+    std::vector<cudaEvent_t> join(nb, nullptr);
     sbp_status st = SBP_OK;
+    int launches = 0;
     bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int k = 0; ok && k < K; ++k)
+    for (int k = 0; ok && k < nb; ++k)
         ok = cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) == cudaSuccess;
     cudaGraph_t graph = nullptr;
     if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         cudaEventRecord(fork, cap);
-        for (int k = 0; k < K; ++k) cudaStreamWaitEvent(br[k], fork, 0);
-        // largest boxes first, each to the least loaded branch
-        std::vector<int> order(n);
-        for (int i = 0; i < n; ++i) order[i] = i;
+        for (int k = 0; k < nb; ++k) cudaStreamWaitEvent(br[k], fork, 0);
+        // grouped sweeps: one branch per group, three launches each
+        int gb = K;
+        for (const SweepGroup& g : e->groups) {
+            if (!g.use) continue;
+            bool any = false;
+            for (int i : g.boxes) any = any || in(i);
+            if (!any) continue;
+            const sbp_plan_s* p0 = e->plans[g.boxes[0]];
+            SweepArgs a = sweep_args(p0);
+            a.boxes = e->table + g.first;
+            const sbp_status s = launch_sweep(p0, a, (int)g.boxes.size(), br[gb++]);
+            launches += 3;
+            if (s != SBP_OK && st == SBP_OK) st = s;
+        }
+        // the other boxes: largest first, each to the least loaded branch
+        std::vector<int> order;
+        for (int i = 0; i < n; ++i)
+            if (!grouped[i] && in(i)) order.push_back(i);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             const sbp_plan_s* pa = e->plans[a];
             const sbp_plan_s* pb = e->plans[b];
             return (size_t)pa->nx * pa->ny * pa->nz > (size_t)pb->nx * pb->ny * pb->nz;
         });
-        std::vector<double> load(K, 0.0);
+        std::vector<double> load(std::max(K, 1), 0.0);
         for (int i : order) {
             const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
             sbp_plan_s* p = e->plans[i];
             load[k] += (double)p->nx * p->ny * p->nz;
             const int chunk = chunked ? auto_chunk(p) : 0;
+            // five passes for a sweep plan here (its group chose them): chunk -1 keeps solve_t off the sweeps
+            const int c = (p->sweep && chunk == 0) ? -2 : chunk;
             const sbp_status s = f64_of(p)
-                                     ? solve_t<double>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, chunk)
-                                     : solve_t<float>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, chunk);
+                                     ? solve_t<double>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, c)
+                                     : solve_t<float>(p, e->rho[i], e->phi[i], 0.0, br[k], e->s_dev + i, c);
+            launches += launches_per_solve(p, c == -2 ? 0 : chunk, c == -2);
             if (s != SBP_OK && st == SBP_OK) st = s;
         }
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < nb; ++k) {
             cudaEventRecord(join[k], br[k]);
             cudaStreamWaitEvent(cap, join[k], 0);
         }
@@ -1255,7 +1375,7 @@ sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_o
     }
     cudaGraphExec_t exec = nullptr;
     if (ok && st == SBP_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) ok = false;
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < nb; ++k) {
         if (br[k]) cudaStreamDestroy(br[k]);
         if (join[k]) cudaEventDestroy(join[k]);
     }
@@ -1269,47 +1389,145 @@ sbp_status capture_batch(BatchExec* e, int K, bool chunked, cudaGraph_t* graph_o
     }
     *graph_out = graph;
     *exec_out = exec;
+    if (launches_out) *launches_out = launches;
     return SBP_OK;
 }
 
-// Build the executor's graph, choosing K by timing when not forced.  The
-// caller holds g_exec_mu.
+// ---- remembered tuning choices (per batch shape and GPU)
+struct TuneChoice {
+    std::vector<char> group_use;
+    int branches = 1, chunked = 0;
+};
+std::vector<std::pair<std::string, TuneChoice>> g_tune_memo;
+
+std::string tune_key(const BatchExec* e) {
+    std::string key;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, e->device) == cudaSuccess) {
+        key = prop.name;
+    } else {
+        cudaGetLastError();
+        key = "gpu";
+    }
+    for (char& c : key)
+        if (c == ' ' || c == '\t' || c == '|') c = '_';
+    for (const sbp_plan_s* p : e->plans) {
+        char buf[96];
+        std::snprintf(buf, sizeof(buf), "|%dx%dx%d:%d:%d%d%d%d", p->nx, p->ny, p->nz, (int)p->dtype, p->sweep ? 1 : 0,
+                      p->frame, p->method, p->pad);
+        key += buf;
+    }
+    return key;
+}
+
+bool tune_lookup(const std::string& key, TuneChoice* out) {
+    for (const auto& kv : g_tune_memo)
+        if (kv.first == key) {
+            *out = kv.second;
+            return true;
+        }
+    const char* path = std::getenv("SBP_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    std::vector<char> line(1 << 16);
+    bool found = false;
+    while (std::fgets(line.data(), (int)line.size(), f)) {
+        std::string s(line.data());
+        const size_t tab = s.find('\t');
+        if (tab == std::string::npos || s.compare(0, tab, key) != 0 || tab != key.size()) continue;
+        TuneChoice c;
+        const char* v = s.c_str() + tab + 1;
+        int used = 0;
+        if (std::sscanf(v, "%d %d%n", &c.branches, &c.chunked, &used) < 2) continue;
+        v += used;
+        while (*v == ' ') ++v;
+        for (; *v == '0' || *v == '1'; ++v) c.group_use.push_back(*v == '1');
+        *out = c;
+        found = true;
+    }
+    std::fclose(f);
+    if (found) g_tune_memo.push_back({key, *out});
+    return found;
+}
+
+void tune_store(const std::string& key, const TuneChoice& c) {
+    g_tune_memo.push_back({key, c});
+    const char* path = std::getenv("SBP_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::string use;
+    for (char u : c.group_use) use += u ? '1' : '0';
+    std::fprintf(f, "%s\t%d %d %s\n", key.c_str(), c.branches, c.chunked, use.c_str());
+    std::fclose(f);
+}
+
+// Time one graph: mean ms of 3 replays after one warm-up replay.
+sbp_status time_graph(cudaGraphExec_t x, cudaStream_t st, cudaEvent_t a, cudaEvent_t b, float* ms) {
+    cudaGraphLaunch(x, st);
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 3; ++r) cudaGraphLaunch(x, st);
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return SBP_ERR_CUDA;
+    }
+    *ms /= 3.f;
+    return SBP_OK;
+}
+
+// Build the executor's graph, choosing the schedule of each group, K and the
+// chunking by timing when neither forced nor remembered.  The caller holds
+// g_exec_mu and has copied the shear parameters to e->s_dev.
 sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
     const int n = (int)e->plans.size();
-    // The same plans with other buffers (double-buffered input and output):
-    // the branch count and chunking depend on the boxes only, so take the
-    // existing executor's choice instead of timing the candidates again.
-    for (const BatchExec* c : g_execs) {
-        if (c == e || !c->exec || c->plans != e->plans) continue;
+    sbp_status s = build_groups(e, e->phi, st);
+    if (s != SBP_OK) return s;
+    auto finish = [&](const TuneChoice& c) -> sbp_status {
+        for (size_t g = 0; g < e->groups.size(); ++g)
+            e->groups[g].use = g < c.group_use.size() ? c.group_use[g] != 0 : true;
+        e->branches = c.branches;
+        e->chunked = c.chunked;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
-        const sbp_status s = capture_batch(e, c->branches, c->chunked != 0, &g, &x);
-        if (s != SBP_OK) return s;
+        int launches = 0;
+        const sbp_status r = capture_batch(e, e->branches, e->chunked != 0, &g, &x, &launches);
+        if (r != SBP_OK) return r;
         e->graph = g;
         e->exec = x;
-        e->branches = c->branches;
-        e->chunked = c->chunked;
-        e->tuned_ms = c->tuned_ms;
+        e->launches = launches;
         return SBP_OK;
+    };
+    // the same plans with other buffers (double buffering) take the existing choice
+    for (const BatchExec* c : g_execs) {
+        if (c == e || !c->exec || c->plans != e->plans) continue;
+        TuneChoice ch;
+        for (const SweepGroup& g : c->groups) ch.group_use.push_back(g.use);
+        ch.branches = c->branches;
+        ch.chunked = c->chunked;
+        e->tuned_ms = c->tuned_ms;
+        return finish(ch);
     }
+    const std::string key = tune_key(e);
+    TuneChoice memo;
+    const char* env_k = std::getenv("SBP_BATCH_BRANCHES");
+    const char* env_c = std::getenv("SBP_BATCH_CHUNK");
+    const char* env_s = std::getenv("SBP_BATCH_SCHEDULE");  // 1: five passes everywhere, 2: grouped sweeps
+    if (!env_k && !env_c && !env_s && tune_lookup(key, &memo) && memo.group_use.size() == e->groups.size())
+        return finish(memo);
+
     std::vector<int> cands;
-    if (const char* env = std::getenv("SBP_BATCH_BRANCHES")) {
-        const int k = std::atoi(env);
+    if (env_k) {
+        const int k = std::atoi(env_k);
         if (k >= 1) cands.push_back(std::min(k, std::max(1, n)));
     }
     if (cands.empty())
         for (int k : {1, 2, 4, 8, 16, 32})
             if (k <= std::max(1, n)) cands.push_back(k);
-    cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
-        cudaGetLastError();
-        if (a) cudaEventDestroy(a);
-        return SBP_ERR_CUDA;
-    }
-    // chunked x/y passes only where some box has more than one chunk
     std::vector<int> chunk_modes = {0};
-    if (const char* env = std::getenv("SBP_BATCH_CHUNK")) {
-        chunk_modes = {std::atoi(env) != 0 ? 1 : 0};
+    if (env_c) {
+        chunk_modes = {std::atoi(env_c) != 0 ? 1 : 0};
     } else {
         for (const sbp_plan_s* p : e->plans)
             if (auto_chunk(p) > 0) {
@@ -1317,17 +1535,32 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
                 break;
             }
     }
-    std::vector<std::pair<int, int>> trials;
-    for (int K : cands)
-        for (int c : chunk_modes) trials.push_back({K, c});
+    const bool sched_free = !env_s && !e->groups.empty();
+    if (env_s)
+        for (SweepGroup& g : e->groups) g.use = std::atoi(env_s) != 1;
+    const size_t trials = (sched_free ? 2 * e->groups.size() : 0) + cands.size() * chunk_modes.size();
+    if (trials <= 1) {
+        TuneChoice c;
+        for (const SweepGroup& g : e->groups) c.group_use.push_back(g.use);
+        c.branches = cands[0];
+        c.chunked = chunk_modes[0];
+        return finish(c);
+    }
+
     // The candidate graphs are replayed several times to time them.  They
     // write into temporary outputs, never into the caller's phi: an in-place
     // box (phi == rho) would otherwise be solved again on every replay, and
     // the caller's rho stays untouched.  The chosen configuration is captured
-    // once more on the caller's buffers below and replayed once by the caller.
+    // once more on the caller's buffers and replayed once by the caller.
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        cudaGetLastError();
+        if (a) cudaEventDestroy(a);
+        return SBP_ERR_CUDA;
+    }
     std::vector<void*> caller_phi = e->phi;
     void* scratch = nullptr;
-    if (trials.size() > 1) {
+    {
         std::vector<size_t> offs(n);
         size_t total = 0;
         for (int i = 0; i < n; ++i) {
@@ -1343,70 +1576,94 @@ sbp_status tune_batch(BatchExec* e, cudaStream_t st) {
         }
         for (int i = 0; i < n; ++i) e->phi[i] = static_cast<unsigned char*>(scratch) + offs[i];
     }
-    auto restore = [&]() {
-        e->phi = caller_phi;
-        if (scratch) {
-            cudaStreamSynchronize(st);
-            cudaFree(scratch);
-            scratch = nullptr;
-        }
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
-    };
-    float best = 0.f;
-    for (const auto& tr : trials) {
-        const int K = tr.first;
+    s = build_groups(e, e->phi, st);
+    auto run_trial = [&](int K, bool chunked, const std::vector<char>& mask, float* ms) -> sbp_status {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t x = nullptr;
-        const sbp_status s = capture_batch(e, K, tr.second != 0, &g, &x);
-        if (s != SBP_OK) {
-            restore();
-            return s;
-        }
-        float ms = 0.f;
-        if (trials.size() > 1) {
-            cudaGraphLaunch(x, st);
-            cudaEventRecord(a, st);
-            for (int r = 0; r < 3; ++r) cudaGraphLaunch(x, st);
-            cudaEventRecord(b, st);
-            if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-                cudaGraphExecDestroy(x);
-                cudaGraphDestroy(g);
-                cudaGetLastError();
-                restore();
-                return SBP_ERR_CUDA;
+        sbp_status r = capture_batch(e, K, chunked, &g, &x, nullptr, mask);
+        if (r != SBP_OK) return r;
+        r = time_graph(x, st, a, b, ms);
+        cudaGraphExecDestroy(x);
+        cudaGraphDestroy(g);
+        return r;
+    };
+    // 1. each group alone: grouped sweeps against per-box five-pass kernels
+    if (s == SBP_OK && sched_free) {
+        for (SweepGroup& g : e->groups) {
+            std::vector<char> mask(n, 0);
+            for (int i : g.boxes) mask[i] = 1;
+            float t_sweep = 0.f, t_five = 0.f;
+            g.use = true;
+            if ((s = run_trial(1, false, mask, &t_sweep)) != SBP_OK) break;
+            g.use = false;
+            const int K = (int)std::min<size_t>(16, g.boxes.size());
+            if ((s = run_trial(K, false, mask, &t_five)) != SBP_OK) break;
+            // grouped sweeps take 3 launches for the whole group: keep them unless clearly slower
+            g.use = t_sweep <= 1.02f * t_five;
+            if (std::getenv("SBP_TUNE_LOG")) {
+                const sbp_plan_s* p0 = e->plans[g.boxes[0]];
+                std::fprintf(stderr, "[sbp tune] %zu x %dx%dx%d: grouped sweeps %.3f ms, five passes %.3f ms -> %s\n",
+                             g.boxes.size(), p0->nx, p0->ny, p0->nz, t_sweep, t_five, g.use ? "sweeps" : "five");
             }
         }
-        if (!e->exec || ms < best) {
-            if (e->exec) cudaGraphExecDestroy(e->exec);
-            if (e->graph) cudaGraphDestroy(e->graph);
-            e->exec = x;
-            e->graph = g;
-            e->branches = K;
-            e->chunked = tr.second;
-            best = ms;
-        } else {
-            cudaGraphExecDestroy(x);
-            cudaGraphDestroy(g);
+    }
+    // 2. the whole graph: branch count and chunking
+    float best = 0.f;
+    TuneChoice choice;
+    bool have = false;
+    for (int K : cands) {
+        for (int c : chunk_modes) {
+            if (s != SBP_OK) break;
+            float ms = 0.f;
+            if ((s = run_trial(K, c != 0, {}, &ms)) != SBP_OK) break;
+            if (std::getenv("SBP_TUNE_LOG"))
+                std::fprintf(stderr, "[sbp tune] whole batch, K = %d, chunked = %d: %.3f ms\n", K, c, ms);
+            if (!have || ms < best) {
+                have = true;
+                best = ms;
+                choice.branches = K;
+                choice.chunked = c;
+            }
         }
     }
-    e->tuned_ms = best / 3.f;
-    const bool timed = (scratch != nullptr);
-    restore();
-    if (timed) {
-        // the kept graph wrote into the temporaries: capture it again on the caller's buffers
-        cudaGraphExecDestroy(e->exec);
-        cudaGraphDestroy(e->graph);
-        e->exec = nullptr;
-        e->graph = nullptr;
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t x = nullptr;
-        const sbp_status s = capture_batch(e, e->branches, e->chunked != 0, &g, &x);
-        if (s != SBP_OK) return s;
-        e->graph = g;
-        e->exec = x;
+    // 3. groups interact in the whole graph (their kernels share the SMs): flip
+    //    each group's schedule in turn and keep the flip when the batch is faster
+    if (s == SBP_OK && sched_free && have) {
+        for (SweepGroup& g : e->groups) {
+            g.use = !g.use;
+            float ms = 0.f;
+            if ((s = run_trial(choice.branches, choice.chunked != 0, {}, &ms)) != SBP_OK) break;
+            const bool keep = ms < 0.99f * best;
+            if (std::getenv("SBP_TUNE_LOG")) {
+                const sbp_plan_s* p0 = e->plans[g.boxes[0]];
+                std::fprintf(stderr, "[sbp tune] whole batch with %dx%dx%d on %s: %.3f ms%s\n", p0->nx, p0->ny, p0->nz,
+                             g.use ? "sweeps" : "five passes", ms, keep ? " (kept)" : "");
+            }
+            if (keep)
+                best = ms;
+            else
+                g.use = !g.use;
+        }
     }
-    return SBP_OK;
+    for (const SweepGroup& g : e->groups) choice.group_use.push_back(g.use);
+    if (std::getenv("SBP_TUNE_LOG")) {
+        std::fprintf(stderr, "[sbp tune] choice: K = %d, chunked = %d, groups:", choice.branches, choice.chunked);
+        for (size_t g = 0; g < e->groups.size(); ++g) {
+            const sbp_plan_s* p0 = e->plans[e->groups[g].boxes[0]];
+            std::fprintf(stderr, " %dx%dx%d=%s", p0->nx, p0->ny, p0->nz, e->groups[g].use ? "sweeps" : "five");
+        }
+        std::fprintf(stderr, " (%.3f ms)\n", best);
+    }
+    e->phi = caller_phi;
+    cudaStreamSynchronize(st);
+    cudaFree(scratch);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (s != SBP_OK) return s;
+    if ((s = build_groups(e, e->phi, st)) != SBP_OK) return s;
+    e->tuned_ms = best;
+    if (!env_k && !env_c && !env_s) tune_store(key, choice);
+    return finish(choice);
 }
 
 template <typename T>
@@ -1886,6 +2143,63 @@ sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, doubl
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return f64_of(p) ? launch_stage<double>(p, stage, in, out, t, st, false)
                      : launch_stage<float>(p, stage, in, out, t, st, false);
+}
+
+sbp_status sbp_batch_info(int nbox, const sbp_plan* plans, const void* const* rho, void* const* phi,
+                          int* launches, int* grouped_boxes) {
+    if (nbox <= 0 || !plans || !rho || !phi) return SBP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    for (const BatchExec* c : g_execs) {
+        if ((int)c->plans.size() != nbox) continue;
+        bool same = true;
+        for (int i = 0; same && i < nbox; ++i)
+            same = c->plans[i] == plans[i] && c->rho[i] == rho[i] && c->phi[i] == phi[i];
+        if (!same) continue;
+        if (launches) *launches = c->launches;
+        if (grouped_boxes) {
+            int g = 0;
+            for (const SweepGroup& s : c->groups)
+                if (s.use) g += (int)s.boxes.size();
+            *grouped_boxes = g;
+        }
+        return SBP_OK;
+    }
+    return SBP_ERR_INVALID_ARG;
+}
+
+sbp_status sbp_batch_run_stage(int nbox, const sbp_plan* plans, const void* const* rho, void* const* phi, int nx,
+                               int ny, int nz, int stage, void* stream) {
+    if (nbox <= 0 || !plans || !rho || !phi) return SBP_ERR_INVALID_ARG;
+    if (stage < SBP_STAGE_SWEEP_FORWARD || stage > SBP_STAGE_SWEEP_INVERSE) return SBP_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_exec_mu);
+    for (const BatchExec* c : g_execs) {
+        if ((int)c->plans.size() != nbox) continue;
+        bool same = true;
+        for (int i = 0; same && i < nbox; ++i)
+            same = c->plans[i] == plans[i] && c->rho[i] == rho[i] && c->phi[i] == phi[i];
+        if (!same) continue;
+        for (const SweepGroup& g : c->groups) {
+            const sbp_plan_s* p0 = c->plans[g.boxes[0]];
+            if (!g.use || p0->nx != nx || p0->ny != ny || p0->nz != nz) continue;
+            DeviceGuard dg(p0->device);
+            if (!dg.ok) return SBP_ERR_CUDA;
+            cudaStream_t st = static_cast<cudaStream_t>(stream);
+            SweepArgs a = sweep_args(p0);
+            a.boxes = c->table + g.first;
+            const SweepKernels& k = p0->sk;
+            const int ablocks = (p0->nz / k.za) * k.rb;
+            const unsigned nb = (unsigned)g.boxes.size();
+            if (stage == SBP_STAGE_SWEEP_FORWARD)
+                k.fwd<<<dim3((unsigned)(a.green_blocks + ablocks), nb), k.nta, k.smem_ac, st>>>(a);
+            else if (stage == SBP_STAGE_SWEEP_MIDDLE)
+                k.mid<<<dim3((unsigned)(k.ra * k.nga + 1), nb), k.ntb, k.smem_b, st>>>(a);
+            else
+                k.inv<<<dim3((unsigned)ablocks, nb), k.nta, k.smem_ac, st>>>(a);
+            return launch_status();
+        }
+        return SBP_ERR_INVALID_ARG;
+    }
+    return SBP_ERR_INVALID_ARG;
 }
 
 sbp_status sbp_plan_query(sbp_plan p, int what, double* value) {

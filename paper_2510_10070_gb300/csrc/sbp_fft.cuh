@@ -680,6 +680,93 @@ __device__ __forceinline__ void fft_static(cpx<T> (&v)[NCOL][E], int t, const cp
     }
 }
 
+// ---------------------------------------------------------------------------
+// Stage-ordered twiddles.  A twiddled stage s (span Ns > 1, radix R) reads
+// ω_N^{jm·r·TWS} for r < R and jm = j mod Ns; with lanes running along the
+// transform (consecutive jm) the natural table index jm·r·TWS strides the
+// banks by r.  The stage table holds the same values at [r - 1][jm], so that
+// consecutive lanes read consecutive slots.  Stages are laid out one after
+// the other; stage_tw_offset gives where stage s starts.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int stage_tw_offset(int N, int E, int S) {
+    int off = 0;
+    for (int s = 1; s < S; ++s) off += (static_radix(N, E, s) - 1) * static_ns(N, E, s);
+    return off;
+}
+__host__ __device__ constexpr int stage_tw_size(int N, int E) { return stage_tw_offset(N, E, static_nstage(N, E)); }
+
+// Fill the stage table from the natural table twg[k] = ω_N^k (global memory).
+template <int N, int E, typename T>
+__device__ __forceinline__ void build_stage_twiddles(cpx<T>* __restrict__ dst, const cpx<T>* __restrict__ twg) {
+    constexpr int NST = static_nstage(N, E);
+    static_for<1, NST>([&](auto sc) {
+        constexpr int S = decltype(sc)::value;
+        constexpr int R = static_radix(N, E, S), Ns = static_ns(N, E, S), TWS = N / (Ns * R);
+        constexpr int off = stage_tw_offset(N, E, S);
+        for (int i = threadIdx.x; i < (R - 1) * Ns; i += blockDim.x) {
+            const int r = i / Ns + 1, jm = i - (r - 1) * Ns;
+            dst[off + i] = twg[(jm * r * TWS) % N];
+        }
+    });
+}
+
+// One radix-R stage as stage_static, reading the stage table.
+template <int R, int E, int NCOL, int Ns, int TF, int OFF, bool LAST, typename T, typename BUF>
+__device__ __forceinline__ void stage_static_st(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ twS,
+                                                const BUF (&buf)[NCOL]) {
+    constexpr int B = E / R;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int j = t + TF * u;
+        const int jm = j % Ns;
+        const int base = (j - jm) * R + jm;
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+            cpx<T> x[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = v[c][u + r * B];
+            if constexpr (Ns > 1) {
+                DftTw<R, T>::run(x, [&](int r) { return twS[OFF + (r - 1) * Ns + jm]; });
+            } else {
+                Dft<R, T>::run(x);
+            }
+            if constexpr (LAST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[c][u + r * B] = x[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) buf[c][base + r * Ns] = x[r];
+            }
+        }
+    }
+}
+
+// fft_static with the stage table (build_stage_twiddles) instead of the natural one.
+template <int N, int E, int S, int NCOL, typename T, typename BUF>
+__device__ __forceinline__ void fft_static_st(cpx<T> (&v)[NCOL][E], int t, const cpx<T>* __restrict__ twS,
+                                              const BUF (&buf)[NCOL]) {
+    constexpr int NST = static_nstage(N, E);
+    static_assert(NST > 0 && NST <= kMaxStages, "length not supported by the radix set");
+    if constexpr (S < NST) {
+        constexpr int R = static_radix(N, E, S);
+        constexpr int Ns = static_ns(N, E, S);
+        constexpr int TF = N / E;
+        constexpr bool LAST = (S + 1 == NST);
+        constexpr int OFF = stage_tw_offset(N, E, S);
+        if constexpr (!LAST) __syncthreads();
+        stage_static_st<R, E, NCOL, Ns, TF, OFF, LAST, T, BUF>(v, t, twS, buf);
+        if constexpr (!LAST) {
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) v[c][e] = buf[c][t + TF * e];
+            }
+        }
+        fft_static_st<N, E, S + 1, NCOL, T, BUF>(v, t, twS, buf);
+    }
+}
+
 // Forward length-M transform of data whose upper half is zero: thread t holds
 // v[e] = x[t + Tf·e] with v[e] = 0 for e ≥ E/2 (never read).  The first
 // stage must have radix E (one butterfly per thread) so that exactly its

@@ -18,7 +18,7 @@
 //       inverse (as k_z_padded); the inverse y transform's first stage
 //       (radix RB over r', on the conjugated data, no twiddle) follows and
 //       output k' is stored at S[k][a][k'][z], in place.  One extra block per
-//       box convolves the FP64 plane sums with the k = 0 kernel.
+//       box (the first) convolves the FP64 plane sums with the k = 0 kernel.
 //   pass C (k3_inverse): per (plane group, j): twiddle ω_NY^{j·k} and the
 //       radix-RA stage over k give rows y = j + RB·r of the (conjugated)
 //       inverse y transform; the x inverse (Hermitian merge, c2r) follows and
@@ -43,22 +43,34 @@ __host__ __device__ constexpr int sweep_ra(int NY) {
 }
 
 __host__ __device__ constexpr int sweep_stage_pitch(int need, int ZA) {
-    // plane stride of the staging buffer: at least `need`, and ≡ 16/ZA (mod 16)
-    // (odd for ZA ≥ 16) so that the ZA planes of one warp access fall in
-    // different banks
-    const int q = ZA >= 16 ? 1 : 16 / ZA;
+    // plane stride (16-byte units) of the staging buffer: at least `need`,
+    // and ≡ 8/ZA (mod 8) (odd for ZA ≥ 8) so that the ZA planes of one warp
+    // access fall in different banks
+    const int q = ZA >= 8 ? 1 : 8 / ZA;
     int s = need;
-    while (s % 16 != q) ++s;
+    while (s % 8 != q) ++s;
     return s;
 }
 
-// Planes per pass-A/C block: the largest divisor of NZ whose row pairs fit
-// 256 threads in whole warps (per = threads of one plane's RA/2 row pairs).
+// Planes per pass-A/C block (per = threads of one plane's RA/2 row pairs):
+// the largest divisor of NZ whose row pairs fit 256 threads in whole warps,
+// unless that gives fewer than 4 planes: passes A and C move runs of ZA
+// consecutive z per (k, a, j), and runs under 32 bytes (ZA < 4) fill only
+// part of each sector and multiply the L1 wavefronts, so blocks then take up
+// to 512 threads to reach 4 planes.
 __host__ __device__ constexpr int sweep_za(int NZ, int per) {
+    for (int za = per > 0 ? 256 / per : 0; za >= 4; --za)
+        if (NZ % za == 0 && (za * per) % 32 == 0) return za;
+    for (int za = 4; per > 0 && za * per <= 512; ++za)
+        if (NZ % za == 0 && (za * per) % 32 == 0) return za;
     for (int za = per > 0 ? 256 / per : 0; za >= 1; --za)
         if (NZ % za == 0 && (za * per) % 32 == 0) return za;
     return 0;
 }
+
+// Resident blocks per SM the passes A and C aim for: 512-thread blocks two
+// (64 registers), smaller ones as many as fit 64 registers (or 8).
+__host__ __device__ constexpr int sweep_ac_blocks(int nt) { return nt > 256 ? 2 : (nt <= 128 ? 8 : 4); }
 
 template <int NX, int NY, int NZ>
 struct SweepShape {
@@ -72,8 +84,13 @@ struct SweepShape {
     static constexpr int PA = ZA * RA / 2;
     static constexpr int NTA = PA * TFX;
     static constexpr int RP = padded_row(NX);
-    static constexpr int SP = sweep_stage_pitch(RA * H, ZA);
-    static constexpr int XS = (PA * RP > ZA * SP) ? PA * RP : ZA * SP;  // exchange / staging slots
+    // staging: per plane, RA/2 row pairs of H slots of 16 bytes (X0 and X1 of
+    // one a side by side); SP is the plane stride in those slots
+    static constexpr int SP = sweep_stage_pitch((RA / 2) * H, ZA);
+    static constexpr int XS = (PA * RP > 2 * ZA * SP) ? PA * RP : 2 * ZA * SP;  // complex slots
+    // y-stage items of passes A and C: (plane, a) for a < NX/2, the a = 0 item
+    // also carrying the real a = NX/2 column as its imaginary part
+    static constexpr int ITEMS_AC = ZA * (NX / 2);
     static constexpr size_t smem_ac = (size_t)(NX + XS) * sizeof(cpx<float>) + (size_t)PA * 8;
     // pass B: AG columns a, RB y columns each, TFZ threads per padded column
     static constexpr int M = 2 * NZ;
@@ -83,12 +100,16 @@ struct SweepShape {
     static constexpr int CB = AG * RB;
     static constexpr int NTB = CB * TFZ;
     static constexpr int NGA = (H + AG - 1) / AG;
+    // threads per y-stage item of pass B (1 or 2: a radix-2 split over a lane pair)
+    static constexpr int TPI = NTB / (AG * NZ) >= 2 && RB % 2 == 0 ? 2 : 1;
     static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
-    static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES +
+    static constexpr int WY_BYTES = (RB * (int)sizeof(cpx<float>) + 15) / 16 * 16;  // ω_NY^{k·j}, j < RB
+    static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES + WY_BYTES +
                                      (size_t)xchg_slots<float>(M, CB) * sizeof(cpx<float>);
-    static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 && NTA <= 256 &&
-                               NTA % 32 == 0 && NTB <= 256 && RB * TFZ <= 256 && AG * NZ <= NTB &&
-                               TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32;
+    static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 &&
+                               NTA % 32 == 0 && NTA <= 512 && NTB <= 256 && RB * TFZ <= 256 && AG * NZ <= NTB &&
+                               TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32 && ITEMS_AC % NTA == 0 && PA >= RA &&
+                               (TPI == 1 || (AG * NZ) % 16 == 0);
 };
 
 // Per-box descriptor of a sweep launch (device memory).
@@ -122,11 +143,32 @@ struct SweepArgs {
     int green_blocks;       // pass A: leading blocks per box that fill the Green's table
 };
 
+// Radix-R DFT split over a lane pair (lanes l and l ^ LANE_XOR).  Thread h
+// holds x[n1] = in[2 n1 + h], n1 < R/2, and ends with out[k1 + h R/2]:
+//   out[k1 + (R/2) k2] = A0[k1] + (-1)^k2 ω_R^{k1} A1[k1],  A_h = DFT_{R/2}(x of h).
+// Every lane of the warp must take part (the shuffles use the full mask).
+template <int R, int LANE_XOR>
+__device__ __forceinline__ void dft_pair(cpx<float> (&x)[R / 2], int h) {
+    Dft<R / 2, float>::run(x);
+    static_for<1, R / 2>([&](auto kc) {
+        constexpr int k1 = decltype(kc)::value;
+        const cpx<float> w = twiddle_const<R, k1>(x[k1]);
+        x[k1] = h ? w : x[k1];
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < R / 2; ++k1) {
+        cpx<float> o;
+        o.x = __shfl_xor_sync(0xffffffffu, x[k1].x, LANE_XOR);
+        o.y = __shfl_xor_sync(0xffffffffu, x[k1].y, LANE_XOR);
+        x[k1] = h ? csub(o, x[k1]) : cadd(x[k1], o);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // pass A
 // ---------------------------------------------------------------------------
 template <int NX, int NY, int NZ>
-__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, NY, NZ>::NTA <= 128 ? 8 : 5))
+__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(SweepShape<NX, NY, NZ>::NTA))
     k3_forward(SweepArgs A) {
     using SH = SweepShape<NX, NY, NZ>;
     constexpr int RA = SH::RA, RB = SH::RB, H = SH::H, EX = SH::EX, TFX = SH::TFX, ZA = SH::ZA;
@@ -157,7 +199,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
     cpx<float>* xb = tw + NX;
     FF* psum = reinterpret_cast<FF*>(xb + XS);
     const int tid = threadIdx.x;
-    for (int i = tid; i < NX; i += SH::NTA) tw[i] = A.twx[i];
+    build_stage_twiddles<NX, EX, float>(tw, A.twx);  // the x transform's stage table (fits in NX slots)
 
     const int t = tid % TFX, c = tid / TFX;
     const int zl = c / (RA / 2), p = c % (RA / 2);
@@ -188,7 +230,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
     }
     __syncthreads();  // twiddles visible
     const SmemRow<float> buf[1] = {{xb + c * RP, 0}};
-    fft_static<NX, EX, 0, 1, float>(v, t, tw, buf);
+    fft_static_st<NX, EX, 0, 1, float>(v, t, tw, buf);
 
     // Hermitian split of the paired transform (Z[n-k] is element E-1-e of lane
     // TFX-t of the same pair, or of lane 0 itself): X0 = (Z[k] + conj Z[n-k])/2,
@@ -199,11 +241,11 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
         for (int q = 0; q < RA / 2; ++q) tot = ff_add(tot, psum[tid * (RA / 2) + q]);
         if (B.tile_sums != nullptr) B.tile_sums[(size_t)(z0 + tid) * RB + j] = (double)tot.hi + (double)tot.lo;
     }
+    float4* st4 = reinterpret_cast<float4*>(xb);  // staging: [plane][pair][a], X0 and X1 side by side
     {
         const int lane = tid & 31;
         const int src = lane - t + ((TFX - t) & (TFX - 1));
-        cpx<float>* o0 = xb + zl * SP + (2 * p) * H;
-        cpx<float>* o1 = o0 + H;
+        float4* o = st4 + zl * SP + p * H;
         const float half = 0.5f;
 #pragma unroll
         for (int e = 0; e <= EX / 2; ++e) {
@@ -216,23 +258,52 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
             const cpx<float> Az = v[0][e];
             if (e < EX / 2 || t == 0) {
                 const int k = t + TFX * e;
-                o0[k] = {(Az.x + Bz.x) * half, (Az.y + Bz.y) * half};
-                o1[k] = {(Az.y - Bz.y) * half, (Bz.x - Az.x) * half};
+                o[k] = make_float4((Az.x + Bz.x) * half, (Az.y + Bz.y) * half, (Az.y - Bz.y) * half,
+                                   (Bz.x - Az.x) * half);
             }
         }
     }
     __syncthreads();
-    // y stage 1: for every (z, a) the radix-RA DFT over the rows r
+    // y stage 1: for every (z, a) the radix-RA DFT over the rows r.  The a = 0
+    // and a = NX/2 columns are real, so one item transforms both at once
+    // (a = 0 as the real part, a = NX/2 as the imaginary part) and separates
+    // them by the Hermitian symmetry of each: A[k] = (C[k] + conj C[-k]) / 2,
+    // B[k] = (C[k] - conj C[-k]) / 2i.
     cpx<float>* __restrict__ S = B.S;
-    for (int i = tid; i < ZA * H; i += SH::NTA) {
+    constexpr size_t KS = (size_t)H * RB * NZ;  // stride of k in S
+#pragma unroll 1
+    for (int i = tid; i < SH::ITEMS_AC; i += SH::NTA) {
         const int zi = i % ZA, a = i / ZA;
         cpx<float> x[RA];
+        const float4* row = st4 + zi * SP;
 #pragma unroll
-        for (int r = 0; r < RA; ++r) x[r] = xb[zi * SP + r * H + a];
+        for (int q = 0; q < RA / 2; ++q) {
+            const float4 f = row[q * H + a];
+            x[2 * q] = {f.x, f.y};
+            x[2 * q + 1] = {f.z, f.w};
+        }
+        if (a == 0) {
+#pragma unroll
+            for (int q = 0; q < RA / 2; ++q) {
+                const float4 g = row[q * H + NX / 2];
+                x[2 * q].y = g.x;
+                x[2 * q + 1].y = g.z;
+            }
+        }
         Dft<RA, float>::run(x);
         cpx<float>* dst = S + ((size_t)a * RB + j) * NZ + z0 + zi;
+        if (a != 0) {
 #pragma unroll
-        for (int k = 0; k < RA; ++k) dst[(size_t)k * H * RB * NZ] = x[k];
+            for (int k = 0; k < RA; ++k) dst[k * KS] = x[k];
+        } else {
+            cpx<float>* dstN = S + ((size_t)(NX / 2) * RB + j) * NZ + z0 + zi;
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                const cpx<float> c = x[k], d = x[(RA - k) % RA];
+                dst[k * KS] = {0.5f * (c.x + d.x), 0.5f * (c.y - d.y)};
+                dstN[k * KS] = {0.5f * (c.y + d.y), 0.5f * (d.x - c.x)};
+            }
+        }
     }
 }
 
@@ -250,10 +321,14 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<float>* twM = reinterpret_cast<cpx<float>*>(smem_raw);
     GreenT<float>* gm = reinterpret_cast<GreenT<float>*>(twM + M);
-    cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
+    cpx<float>* wy = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
+    cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(wy) + SH::WY_BYTES);
     const int tid = threadIdx.x;
-    if ((int)blockIdx.x == RA * NGA) {
-        // the FP64 mean mode: vk0[i] = coef Σ_j c00[i - j + NZ - 1] S[j] from the plane sums
+    if (blockIdx.x == 0) {
+        // the FP64 mean mode: vk0[i] = coef Σ_j c00[i - j + NZ - 1] S[j] from the
+        // plane sums (O(NZ²) at GB300's 1/64-rate FP64: the first block of each
+        // box's row, so that it overlaps the transform blocks instead of
+        // trailing them)
         if (B.vk0 != nullptr) {
             ZArgs za;
             za.tile_sums = B.tile_sums;
@@ -265,9 +340,10 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
         }
         return;
     }
-    const int k = (int)blockIdx.x / NGA, ag = (int)blockIdx.x % NGA;
+    const int k = ((int)blockIdx.x - 1) / NGA, ag = ((int)blockIdx.x - 1) % NGA;
     const int a0 = ag * AG;
     for (int i = tid; i < M; i += SH::NTB) twM[i] = A.twM[i];
+    if (tid < RB) wy[tid] = A.twy[(k * tid) % NY];
     if (tid < CB) {
         const int a = a0 + tid / RB, b = k + RA * (tid % RB);
         GreenT<float> g = {};
@@ -279,27 +355,35 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     cpx<float>* __restrict__ S = B.S;
     const size_t tile = ((size_t)k * H + a0) * RB * NZ;  // this block's [AG][RB][NZ] tile
     // y stage 2 (forward): item (al, z) takes twiddle ω_NY^{k·j} and the
-    // radix-RB DFT over j; output r' is column al·RB + r' (b = k + RA·r')
-    const int zi = tid % NZ, al = tid / NZ;
-    const bool item = tid < AG * NZ && a0 + al < H;
-    if (item) {
-        cpx<float> x[RB];
+    // radix-RB DFT over j; output r' is column al·RB + r' (b = k + RA·r').
+    // With TPI = 2 the two half-warps share the same 16 items (lane l and
+    // l ^ 16, dft_pair), so that each half-warp's accesses stay unit-stride.
+    constexpr int TPI = SH::TPI, NV = RB / TPI;
+    const int item = TPI == 2 ? (tid >> 5) * 16 + (tid & 15) : tid;
+    const int h = TPI == 2 ? ((tid >> 4) & 1) : 0;
+    __syncthreads();  // wy visible
+    const int zi = item % NZ, al = item / NZ;
+    const bool in_range = item < AG * NZ;  // warp-uniform: items are contiguous in tid
+    const bool valid = in_range && a0 + al < H;
+    if (in_range) {
+        cpx<float> x[NV];
         const cpx<float>* src = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-        for (int jj = 0; jj < RB; ++jj) x[jj] = src[(size_t)jj * NZ];
-#pragma unroll
-        for (int jj = 1; jj < RB; ++jj) x[jj] = cmul(x[jj], A.twy[(k * jj) % NY]);
-        Dft<RB, float>::run(x);
-#pragma unroll
-        for (int rr = 0; rr < RB; ++rr) {
-            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
-            col[zi] = x[rr];
+        for (int n1 = 0; n1 < NV; ++n1) {
+            const int jj = TPI * n1 + h;
+            cpx<float> v0 = {0.f, 0.f};
+            if (valid) v0 = src[(size_t)jj * NZ];
+            x[n1] = cmul(v0, wy[jj]);
         }
-    } else if (tid < AG * NZ) {
+        if constexpr (TPI == 2) {
+            dft_pair<RB, 16>(x, h);
+        } else {
+            Dft<RB, float>::run(x);
+        }
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr) {
-            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
-            col[zi] = {0.f, 0.f};
+        for (int k1 = 0; k1 < NV; ++k1) {
+            const XchgCol<float, CB> col = {xb + al * RB + k1 + h * NV, 0};
+            col[zi] = x[k1];
         }
     }
     __syncthreads();
@@ -343,17 +427,23 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
 #pragma unroll
     for (int e = 0; e < EZ / 2; ++e) buf[0][t + TFZ * e] = v[0][e];
     __syncthreads();
-    if (item) {
-        cpx<float> x[RB];
+    if (in_range) {
+        cpx<float> x[NV];
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr) {
-            const XchgCol<float, CB> col = {xb + al * RB + rr, 0};
-            x[rr] = col[zi];
+        for (int n1 = 0; n1 < NV; ++n1) {
+            const XchgCol<float, CB> col = {xb + al * RB + TPI * n1 + h, 0};
+            x[n1] = col[zi];
         }
-        Dft<RB, float>::run(x);
-        cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
+        if constexpr (TPI == 2) {
+            dft_pair<RB, 16>(x, h);
+        } else {
+            Dft<RB, float>::run(x);
+        }
+        if (valid) {
+            cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-        for (int kp = 0; kp < RB; ++kp) dst[(size_t)kp * NZ] = x[kp];
+            for (int k1 = 0; k1 < NV; ++k1) dst[(size_t)(k1 + h * NV) * NZ] = x[k1];
+        }
     }
 }
 
@@ -361,7 +451,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
 // pass C
 // ---------------------------------------------------------------------------
 template <int NX, int NY, int NZ>
-__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, NY, NZ>::NTA <= 128 ? 8 : 4))
+__global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(SweepShape<NX, NY, NZ>::NTA))
     k3_inverse(SweepArgs A) {
     using SH = SweepShape<NX, NY, NZ>;
     constexpr int RA = SH::RA, RB = SH::RB, H = SH::H, EX = SH::EX, TFX = SH::TFX, ZA = SH::ZA;
@@ -376,21 +466,46 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
     cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* xb = tw + NX;
     const int tid = threadIdx.x;
-    for (int i = tid; i < NX; i += SH::NTA) tw[i] = A.twx[i];
+    build_stage_twiddles<NX, EX, float>(tw, A.twx);
+    cpx<float>* wy = xb + SH::XS;  // ω_NY^{j·k}, k < RA (PA ≥ RA slots after the staging)
+    if (tid < RA) wy[tid] = A.twy[(j * tid) % NY];
+    __syncthreads();
     // y stage 2 of the inverse: twiddle ω_NY^{j·k} and the radix-RA DFT over k
-    // give rows j + RB·r of the conjugated inverse y transform
+    // give rows j + RB·r of the conjugated inverse y transform.  The a = 0 and
+    // a = NX/2 columns come out real, so one item transforms both (as u + i v)
+    // and keeps the real and imaginary parts of the result.
     const cpx<float>* __restrict__ S = B.S;
-    for (int i = tid; i < ZA * H; i += SH::NTA) {
+    float4* st4 = reinterpret_cast<float4*>(xb);  // staging: [plane][pair][a], rows 2q and 2q+1 side by side
+    constexpr size_t KS = (size_t)H * RB * NZ;
+#pragma unroll 1
+    for (int i = tid; i < SH::ITEMS_AC; i += SH::NTA) {
         const int zi = i % ZA, a = i / ZA;
         cpx<float> x[RA];
         const cpx<float>* src = S + ((size_t)a * RB + j) * NZ + z0 + zi;
 #pragma unroll
-        for (int k = 0; k < RA; ++k) x[k] = src[(size_t)k * H * RB * NZ];
+        for (int k = 0; k < RA; ++k) x[k] = src[k * KS];
+        if (a == 0) {
+            const cpx<float>* srcN = S + ((size_t)(NX / 2) * RB + j) * NZ + z0 + zi;
 #pragma unroll
-        for (int k = 1; k < RA; ++k) x[k] = cmul(x[k], A.twy[(j * k) % NY]);
+            for (int k = 0; k < RA; ++k) {
+                const cpx<float> u = x[k], w = srcN[k * KS];
+                x[k] = {u.x - w.y, u.y + w.x};
+            }
+        }
+#pragma unroll
+        for (int k = 1; k < RA; ++k) x[k] = cmul(x[k], wy[k]);
         Dft<RA, float>::run(x);
+        float4* row = st4 + zi * SP;
+        if (a != 0) {
 #pragma unroll
-        for (int r = 0; r < RA; ++r) xb[zi * SP + r * H + a] = x[r];
+            for (int q = 0; q < RA / 2; ++q) row[q * H + a] = make_float4(x[2 * q].x, x[2 * q].y, x[2 * q + 1].x, x[2 * q + 1].y);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RA / 2; ++q) {
+                row[q * H] = make_float4(x[2 * q].x, 0.f, x[2 * q + 1].x, 0.f);
+                row[q * H + NX / 2] = make_float4(x[2 * q].y, 0.f, x[2 * q + 1].y, 0.f);
+            }
+        }
     }
     __syncthreads();
 
@@ -400,26 +515,26 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, (SweepShape<NX, N
     const int t = tid % TFX, c = tid / TFX;
     const int zl = c / (RA / 2), p = c % (RA / 2);
     const int z = z0 + zl;
-    const cpx<float>* w0 = xb + zl * SP + (2 * p) * H;
-    const cpx<float>* w1 = w0 + H;
+    const float4* w = st4 + zl * SP + p * H;
     cpx<float> v[1][EX];
 #pragma unroll
     for (int e = 0; e < EX; ++e) {
         const int k = t + TFX * e;
         if (2 * k <= NX) {
-            cpx<float> c0 = w0[k], c1 = w1[k];
+            const float4 f = w[k];
+            cpx<float> c0 = {f.x, f.y}, c1 = {f.z, f.w};
             if (k == 0 || 2 * k == NX) {
                 c0.y = 0.f;
                 c1.y = 0.f;
             }
             v[0][e] = {c0.x + c1.y, c0.y - c1.x};
         } else {
-            const cpx<float> c0 = w0[NX - k], c1 = w1[NX - k];
-            v[0][e] = {c0.x - c1.y, -c0.y - c1.x};
+            const float4 f = w[NX - k];
+            v[0][e] = {f.x - f.w, -f.y - f.z};
         }
     }
     const SmemRow<float> buf[1] = {{xb + c * RP, 0}};
-    fft_static<NX, EX, 0, 1, float>(v, t, tw, buf);  // its first exchange follows a barrier
+    fft_static_st<NX, EX, 0, 1, float>(v, t, tw, buf);  // its first exchange follows a barrier
     float add_hi = 0.f, add_lo = 0.f;
     if (B.vk0 != nullptr) {
         const double vv = B.vk0[z];

@@ -94,6 +94,10 @@ SIGNATURES = {
     "sbp_solve_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double,
                                    _c_double, _vp, _vp, _c_double, _vp]),
     "sbp_plan_query": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_double)]),
+    "sbp_batch_info": (_c_int, [_c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "sbp_batch_run_stage": (_c_int, [_c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _c_int,
+                                     _c_int, _c_int, _c_int, _vp]),
 }
 
 _lib = None
@@ -255,9 +259,28 @@ def solve_batched(plans, rhos, phis, ts, stream=None):
     return phis
 
 
-def batched_launches(plans) -> int:
-    """Kernels one sbp_solve_batched call over these plans launches."""
-    return int(sum(p.query(2) for p in plans))
+def batch_info(plans, rhos, phis):
+    """(kernels per call, boxes in grouped sweeps) of the cached
+    sbp_solve_batched graph for exactly these plans and buffers."""
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    rp = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in phis])
+    launches, grouped = ctypes.c_int(), ctypes.c_int()
+    _check(lib().sbp_batch_info(n, hp, rp, fp, ctypes.byref(launches), ctypes.byref(grouped)), "sbp_batch_info")
+    return launches.value, grouped.value
+
+
+def batch_run_stage(plans, rhos, phis, shape, stage, stream=None):
+    """One sweep (Stage.SWEEP_*) of the grouped boxes of `shape` (nx, ny, nz)
+    of the cached sbp_solve_batched graph for exactly these plans and buffers."""
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    rp = (ctypes.c_void_p * n)(*[r.data_ptr() for r in rhos])
+    fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in phis])
+    nx, ny, nz = shape
+    _check(lib().sbp_batch_run_stage(n, hp, rp, fp, int(nx), int(ny), int(nz), int(stage), _stream_handle(stream)),
+           f"sbp_batch_run_stage({Stage(stage).name})")
 
 
 def solve_noalloc(rho, phi, Lx, Ly, Lz, q=1.5, Omega=1.0, G=1.0, t=0.0, stream=None):

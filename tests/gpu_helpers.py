@@ -78,3 +78,18 @@ def spec_input(X, dtype):
     if int(dtype) == 0:
         return np.asarray(X, dtype=np.complex128)
     return (X.real.astype(np.float32).astype(np.float64) + 1j * X.imag.astype(np.float32).astype(np.float64))
+
+
+def same_as_a_single_solve(sbp, plan, rho, t, out):
+    """True when a batched box's output equals, bit for bit, a single solve of
+    the same plan on one of the two schedules (the batched executor picks the
+    grouped three sweeps or the five passes per group of boxes by timing)."""
+    import torch
+
+    one = plan.solve(rho, t=t)
+    if torch.equal(out, one):
+        return True
+    other = sbp.Plan(plan.nx, plan.ny, plan.nz, plan.Lx, plan.Ly, plan.Lz, q=plan.q, Omega=plan.Omega, G=plan.G,
+                     dtype=plan.dtype)
+    other.set_option(sbp.Option.SCHEDULE, 1 if plan.schedule_is_sweep() else 0)
+    return bool(torch.equal(out, other.solve(rho, t=t)))

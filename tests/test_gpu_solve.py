@@ -12,7 +12,7 @@ import pytest
 
 import analytic as A
 import oracle as O
-from gpu_helpers import TOL, as_input, parity, rel_l2, to_dev
+from gpu_helpers import TOL, as_input, parity, rel_l2, same_as_a_single_solve, to_dev
 from paper_2510_10070_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -142,7 +142,7 @@ def test_batched_in_place_first_call(sbp, dtype):
         sbp.solve_batched(plans, bufs, bufs, ts)
         torch.cuda.synchronize()
         for i in range(len(plans)):
-            assert torch.equal(bufs[i], singles[i]), (i, ts)
+            assert same_as_a_single_solve(sbp, plans[i], to_dev(rho_np[i], dtype), ts[i], bufs[i]), (i, ts)
         want = O.solve(as_input(rho_np[3], dtype), _params(boxes[3]), ts[3])
         assert rel_l2(bufs[3].double().cpu().numpy(), want) <= TOL[dtype]
         plans[2].set_option(sbp.Option.Z_VARIANT, 0)  # drops the executor: the next call tunes again
@@ -190,10 +190,9 @@ def test_batched_uneven_boxes_repeated_calls(sbp, dtype):
     outs = [torch.empty_like(r) for r in rhos]
     for ts in ([0.1, 2.0, -1.0, 3.3, 7.7], [5.0, 0.0, 0.4, -2.2, 1.9], [0.1, 2.0, -1.0, 3.3, 7.7]):
         sbp.solve_batched(plans, rhos, outs, ts)
-        singles = [plans[i].solve(rhos[i], t=ts[i]) for i in range(len(plans))]
         torch.cuda.synchronize()
         for i in range(len(plans)):
-            assert torch.equal(outs[i], singles[i]), (i, ts)
+            assert same_as_a_single_solve(sbp, plans[i], rhos[i], ts[i], outs[i]), (i, ts)
     # one box against the oracle
     want = O.solve(as_input(rhos[3].double().cpu().numpy(), dtype), _params(boxes[3]), -2.2)
     sbp.solve_batched(plans, rhos, outs, [5.0, 0.0, 0.4, -2.2, 1.9])
@@ -221,7 +220,9 @@ def test_batched_double_buffered(sbp, dtype):
     torch.cuda.synchronize()
     for rhos, outs in sets:
         for i, p in enumerate(plans):
-            assert torch.equal(outs[i], p.solve(rhos[i], t=ts[i])), i
+            assert same_as_a_single_solve(sbp, p, rhos[i], ts[i], outs[i]), i
+    # both buffer sets ran the same schedule (the second executor took the first one's choice)
+    assert sbp.batch_info(plans, *sets[0]) == sbp.batch_info(plans, *sets[1])
 
 
 def test_empty_batch_and_length_mismatch(sbp):
@@ -306,7 +307,9 @@ def test_batch96_as_benchmarked(sbp):
         sbp.solve_batched(plans, rhos, outs, times)
     torch.cuda.synchronize()
     for i, p in enumerate(plans):
-        assert torch.equal(outs[i], p.solve(rhos[i], t=times[i])), i
+        assert same_as_a_single_solve(sbp, p, rhos[i], times[i], outs[i]), i
+    launches, grouped = sbp.batch_info(plans, rhos, outs)
+    assert launches >= 3 and 0 <= grouped <= len(plans)
     rng = np.random.default_rng(96)
     for i in (0, 33, 66, 95):  # 64³, 128²×64, 192²×96, 256²×128
         b = boxes[i]
