@@ -92,6 +92,7 @@ struct sbp_plan_s {
     SweepKernels sk;
     int sweep_green_blocks = 0;
     SweepBox* sweep_box = nullptr;   // this plan's device descriptor (in `tables`)
+    CUtensorMap sweep_tmap;          // its tensor map (also copied into batched descriptors)
     // z-pass geometry: stored columns per row, rows per plane, row pitch
     int zh = 0, zrows = 0, zpitch = 0;
     // physical frame (SBP_OPT_FRAME = 1): y-first passes with the mapping of Sect. 2.1
@@ -562,6 +563,7 @@ sbp_status upload_tables(sbp_plan_s* p) {
         // phi and the shear parameter come with each launch)
         SweepBox d;
         std::memset(&d, 0, sizeof(d));
+        d.err = p->err;
         d.S = reinterpret_cast<cpx<float>*>(p->W);
         d.green = reinterpret_cast<GreenT<float>*>(p->green);
         d.tile_sums = p->tile_sums;
@@ -1059,6 +1061,26 @@ bool configure_sweep(sbp_plan_s* p) {
             return p->schedule != 2;
         }
     }
+    // the half spectrum as a 4D tensor (z, j, a, k) of 8-byte elements for the
+    // TMA path of passes A and C: box (za, 1, nx/2+1, ra)
+    {
+        auto enc = tensor_map_encoder();
+        if (!enc) return p->schedule != 2;
+        const cuuint64_t nz = (cuuint64_t)p->nz, rb = (cuuint64_t)k.rb, h = (cuuint64_t)p->h, ra = (cuuint64_t)k.ra;
+        cuuint64_t dims[4] = {nz, rb, h, ra};
+        cuuint64_t strides[3] = {nz * 8, rb * nz * 8, h * rb * nz * 8};
+        cuuint32_t box[4] = {(cuuint32_t)k.za, 1, (cuuint32_t)p->h, (cuuint32_t)k.ra};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&p->sweep_tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, p->W, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return p->schedule != 2;
+        if (cudaMemcpy(&p->sweep_box->tmap, &p->sweep_tmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return p->schedule != 2;
+        }
+    }
     p->sk = k;
     p->sweep_green_blocks = (p->h * p->ny + k.nta - 1) / k.nta;
     p->sweep = true;
@@ -1073,6 +1095,8 @@ SweepArgs sweep_args(const sbp_plan_s* p) {
     a.twy = static_cast<const cpx<float>*>(p->tw_y);
     a.twM = static_cast<const cpx<float>*>(p->tw_M);
     a.green_blocks = p->sweep_green_blocks;
+    a.budget = p->spin_budget;
+    a.withhold = p->withhold;
     return a;
 }
 
@@ -1271,6 +1295,8 @@ sbp_status build_groups(BatchExec* e, const std::vector<void*>& phi, cudaStream_
             const sbp_plan_s* p = e->plans[i];
             SweepBox d;
             std::memset(&d, 0, sizeof(d));
+            d.tmap = p->sweep_tmap;
+            d.err = p->err;
             d.rho = static_cast<const float*>(e->rho[i]);
             d.phi = static_cast<float*>(phi[i]);
             d.S = reinterpret_cast<cpx<float>*>(p->W);

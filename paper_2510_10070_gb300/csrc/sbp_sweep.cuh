@@ -91,6 +91,7 @@ struct SweepShape {
     // y-stage items of passes A and C: (plane, a) for a < NX/2, the a = 0 item
     // also carrying the real a = NX/2 column as its imaginary part
     static constexpr int ITEMS_AC = ZA * (NX / 2);
+    // twiddles | exchange / staging / TMA box | pass A: pair sums (PA); pass C: ω_NY^{j·k} (RA) and an mbarrier
     static constexpr size_t smem_ac = (size_t)(NX + XS) * sizeof(cpx<float>) + (size_t)PA * 8;
     // pass B: AG columns a, RB y columns each, TFZ threads per padded column
     static constexpr int M = 2 * NZ;
@@ -106,6 +107,13 @@ struct SweepShape {
     static constexpr int WY_BYTES = (RB * (int)sizeof(cpx<float>) + 15) / 16 * 16;  // ω_NY^{k·j}, j < RB
     static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES + WY_BYTES +
                                      (size_t)xchg_slots<float>(M, CB) * sizeof(cpx<float>);
+    // TMA path of passes A and C: the block's box of the half spectrum,
+    // [k < RA][a < H][j: 1][z < ZA], moved by one bulk tensor copy through the
+    // staging region (items in one round, box no larger than the region, z run
+    // a multiple of 16 bytes, every box dimension ≤ 256)
+    static constexpr int BOX = RA * H * ZA;  // complex values
+    static constexpr bool TMA = ITEMS_AC == NTA && BOX <= XS && (ZA * 8) % 16 == 0 && H <= 256 && ZA <= 256 &&
+                                PA >= RA + 1 && (NX * 8) % 128 == 0;
     static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 &&
                                NTA % 32 == 0 && NTA <= 512 && NTB <= 256 && RB * TFZ <= 256 && AG * NZ <= NTB &&
                                TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32 && ITEMS_AC % NTA == 0 && PA >= RA &&
@@ -114,6 +122,10 @@ struct SweepShape {
 
 // Per-box descriptor of a sweep launch (device memory).
 struct SweepBox {
+    // the half spectrum as a 4D tensor (z, j, a, k), 8-byte elements, box
+    // (ZA, 1, H, RA): the TMA path of passes A and C (unused elsewhere)
+    CUtensorMap tmap;
+    int* err;               // status word: set to 1 when a bounded wait gives up
     const float* rho;       // [NZ][NY][NX]
     float* phi;             // [NZ][NY][NX]
     cpx<float>* S;          // half spectrum, [RA][H][RB][NZ]
@@ -141,6 +153,8 @@ struct SweepArgs {
     const cpx<float>* twy;  // e^{-2πi k/NY}, k < NY
     const cpx<float>* twM;  // e^{-2πi k/2NZ}, k < 2NZ
     int green_blocks;       // pass A: leading blocks per box that fill the Green's table
+    long long budget;       // clock cycles a bounded wait may take
+    int withhold;           // test switch: the TMA loads arm no copy, so their waits run out
 };
 
 // Radix-R DFT split over a lane pair (lanes l and l ^ LANE_XOR).  Thread h
@@ -194,7 +208,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     const int bid = (int)blockIdx.x - A.green_blocks;
     const int zg = bid % (NZ / ZA), j = bid / (NZ / ZA);
     const int z0 = zg * ZA;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];  // the TMA box at xb: 128-byte aligned (NX·8 is)
     cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* xb = tw + NX;
     FF* psum = reinterpret_cast<FF*>(xb + XS);
@@ -291,6 +305,31 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
             }
         }
         Dft<RA, float>::run(x);
+        if constexpr (SH::TMA) {
+            // one round of items: stage the outputs in box order [k][a][zi]
+            // (aliasing the staging, hence the barrier) and store the box by TMA
+            cpx<float>* bx = xb;
+            __syncthreads();
+            if (a != 0) {
+#pragma unroll
+                for (int k = 0; k < RA; ++k) bx[(k * H + a) * ZA + zi] = x[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < RA; ++k) {
+                    const cpx<float> c = x[k], d = x[(RA - k) % RA];
+                    bx[(k * H) * ZA + zi] = {0.5f * (c.x + d.x), 0.5f * (c.y - d.y)};
+                    bx[(k * H + NX / 2) * ZA + zi] = {0.5f * (c.y + d.y), 0.5f * (d.x - c.x)};
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_4d(&B.tmap, z0, j, 0, 0, bx);
+                bulk_commit();
+                bulk_wait_read();  // the block's shared memory stays until the copy has read it
+            }
+            continue;
+        }
         cpx<float>* dst = S + ((size_t)a * RB + j) * NZ + z0 + zi;
         if (a != 0) {
 #pragma unroll
@@ -462,14 +501,36 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     const int bid = blockIdx.x;
     const int zg = bid % (NZ / ZA), j = bid / (NZ / ZA);
     const int z0 = zg * ZA;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];  // the TMA box at xb: 128-byte aligned (NX·8 is)
     cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* xb = tw + NX;
     const int tid = threadIdx.x;
-    build_stage_twiddles<NX, EX, float>(tw, A.twx);
     cpx<float>* wy = xb + SH::XS;  // ω_NY^{j·k}, k < RA (PA ≥ RA slots after the staging)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wy + RA);
+    if constexpr (SH::TMA) {
+        // the block's box [k][a][j][z0 .. z0+ZA) of the half spectrum by one TMA load
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            mbar_fence_init();
+            if (!A.withhold) {
+                mbar_arrive_expect_tx(bar, (uint32_t)(SH::BOX * sizeof(cpx<float>)));
+                tma_load_4d(xb, &B.tmap, z0, j, 0, 0, bar);
+            }
+        }
+    }
+    build_stage_twiddles<NX, EX, float>(tw, A.twx);
     if (tid < RA) wy[tid] = A.twy[(j * tid) % NY];
     __syncthreads();
+    if constexpr (SH::TMA) {
+        const bool ok = mbar_wait_bounded(bar, 0, A.budget);
+        if (!__syncthreads_and(ok)) {  // uniform exit: the copy did not arrive in time
+            if (tid == 0 && B.err != nullptr) atomicExch(B.err, 1);
+            // a copy that is only late still targets this block's shared memory:
+            // stay resident (a second bounded wait) until it lands
+            if (!A.withhold) mbar_wait_bounded(bar, 0, A.budget);
+            return;
+        }
+    }
     // y stage 2 of the inverse: twiddle ω_NY^{j·k} and the radix-RA DFT over k
     // give rows j + RB·r of the conjugated inverse y transform.  The a = 0 and
     // a = NX/2 columns come out real, so one item transforms both (as u + i v)
@@ -481,15 +542,29 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     for (int i = tid; i < SH::ITEMS_AC; i += SH::NTA) {
         const int zi = i % ZA, a = i / ZA;
         cpx<float> x[RA];
-        const cpx<float>* src = S + ((size_t)a * RB + j) * NZ + z0 + zi;
+        if constexpr (SH::TMA) {
+            const cpx<float>* bx = xb;  // box [k][a][zi]
 #pragma unroll
-        for (int k = 0; k < RA; ++k) x[k] = src[k * KS];
-        if (a == 0) {
-            const cpx<float>* srcN = S + ((size_t)(NX / 2) * RB + j) * NZ + z0 + zi;
+            for (int k = 0; k < RA; ++k) x[k] = bx[(k * H + a) * ZA + zi];
+            if (a == 0) {
 #pragma unroll
-            for (int k = 0; k < RA; ++k) {
-                const cpx<float> u = x[k], w = srcN[k * KS];
-                x[k] = {u.x - w.y, u.y + w.x};
+                for (int k = 0; k < RA; ++k) {
+                    const cpx<float> u = x[k], w = bx[(k * H + NX / 2) * ZA + zi];
+                    x[k] = {u.x - w.y, u.y + w.x};
+                }
+            }
+            __syncthreads();  // every item has its inputs: the box region becomes the staging
+        } else {
+            const cpx<float>* src = S + ((size_t)a * RB + j) * NZ + z0 + zi;
+#pragma unroll
+            for (int k = 0; k < RA; ++k) x[k] = src[k * KS];
+            if (a == 0) {
+                const cpx<float>* srcN = S + ((size_t)(NX / 2) * RB + j) * NZ + z0 + zi;
+#pragma unroll
+                for (int k = 0; k < RA; ++k) {
+                    const cpx<float> u = x[k], w = srcN[k * KS];
+                    x[k] = {u.x - w.y, u.y + w.x};
+                }
             }
         }
 #pragma unroll

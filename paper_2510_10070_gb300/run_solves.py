@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--method", type=int, default=0, help="1, 2: SASHA (Sect. 2.2)")
     ap.add_argument("--force", action="store_true", help="also take -grad(phi) after each solve")
     ap.add_argument("--schedule", type=int, default=0, help="1: five passes, 2: three sweeps (0: automatic)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="solve this many boxes of the shape per call through sbp_solve_batched")
     args = ap.parse_args(argv)
     nx, ny, nz = (int(v) for v in args.box.lower().split("x"))
     Lx, Ly, Lz = (float(v) for v in args.lengths.split(","))
@@ -52,6 +54,20 @@ def main(argv=None):
                                                                            device="cuda", dtype=torch.float64))
     rho = rho.to(plan.torch_dtype).contiguous()
     phi = torch.empty_like(rho)
+    if args.batch > 0:
+        # one plan per box (same shape), each with its own input and output
+        plans = [plan] + [sbp.Plan(nx, ny, nz, Lx, Ly, Lz, dtype=dt) for _ in range(args.batch - 1)]
+        for p in plans[1:]:
+            if args.schedule:
+                p.set_option(sbp.Option.SCHEDULE, args.schedule)
+        rhos = [rho] + [torch.roll(rho, i, dims=2).contiguous() for i in range(1, args.batch)]
+        phis = [torch.empty_like(r) for r in rhos]
+        ts = [args.t + 0.37 * i for i in range(args.batch)]
+        for _ in range(args.solves):
+            sbp.solve_batched(plans, rhos, phis, ts)
+        torch.cuda.synchronize()
+        print(f"{args.solves} batched calls of {args.batch} x {nx}x{ny}x{nz} ({args.dtype}) done")
+        return
     g = torch.empty((3,) + tuple(rho.shape), dtype=rho.dtype, device="cuda") if args.force else None
     for _ in range(args.solves):
         plan.solve(rho, phi, t=args.t)

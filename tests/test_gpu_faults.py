@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 from gpu_helpers import STAGE_TOL, np_to_spec, rel_l2, spec_input, spec_to_np
+from paper_2510_10070_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -58,3 +59,28 @@ def test_y_pass_tma_and_plain_loads_agree(sbp):
     torch.cuda.synchronize()
     h = nx // 2 + 1
     assert torch.equal(a[..., :h, :], b[..., :h, :])
+
+
+def test_sweep_tma_wait_times_out_and_plan_recovers(sbp):
+    # The three-sweep schedule loads pass C's box of the half spectrum by TMA
+    # (128x128x64 and 256x256x128): with the copy withheld its bounded wait
+    # runs out, the status word reports it and the next solve is correct.
+    import torch
+
+    box = W.Box(128, 128, 64, 8.0, 8.0, 4.0)
+    plan = sbp.Plan(box.nx, box.ny, box.nz, box.Lx, box.Ly, box.Lz, dtype=sbp.DType.F32)
+    plan.set_option(sbp.Option.SCHEDULE, 2)
+    rho = torch.tensor(np.random.default_rng(33).standard_normal((64, 128, 128)) + 1.0, dtype=torch.float32,
+                       device="cuda")
+    plan.set_option(sbp.Option.SPIN_BUDGET, 2e6)
+    plan.set_option(sbp.Option.DEBUG_WITHHOLD_COPY, 1)
+    plan.solve(rho, t=0.4)
+    with pytest.raises(sbp.SbpError) as err:
+        plan.sync_status()
+    assert err.value.status == sbp.Status.DEVICE_TIMEOUT
+    plan.sync_status()
+    plan.set_option(sbp.Option.DEBUG_WITHHOLD_COPY, 0)
+    got = plan.solve(rho, t=0.4).double().cpu().numpy()
+    plan.sync_status()
+    want = O.solve(rho.double().cpu().numpy(), O.SolveParams(box.Lx, box.Ly, box.Lz), 0.4)
+    assert rel_l2(got, want) <= 2e-5
