@@ -39,7 +39,7 @@ namespace sbp {
 // Radix of the y stage fused into the x passes (RA) for a length NY; the
 // other stage (pass B) has radix NY / RA.  0: no split built for NY.
 __host__ __device__ constexpr int sweep_ra(int NY) {
-    return NY == 32 ? 4 : NY == 64 ? 8 : NY == 96 ? 12 : NY == 128 ? 16 : NY == 192 ? 12 : NY == 256 ? 16 : 0;
+    return NY == 32 ? 4 : NY == 64 ? 8 : NY == 96 ? 12 : NY == 128 ? 16 : NY == 192 ? 24 : NY == 256 ? 16 : 0;
 }
 
 __host__ __device__ constexpr int sweep_stage_pitch(int need, int ZA) {
@@ -115,7 +115,7 @@ struct SweepShape {
     static constexpr bool TMA = ITEMS_AC == NTA && BOX <= XS && (ZA * 8) % 16 == 0 && H <= 256 && ZA <= 256 &&
                                 PA >= RA + 1 && (NX * 8) % 128 == 0;
     static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 &&
-                               NTA % 32 == 0 && NTA <= 512 && NTB <= 256 && RB * TFZ <= 256 && AG * NZ <= NTB &&
+                               NTA % 32 == 0 && NTA <= 512 && NTB <= 256 && RB * TFZ <= 256 &&
                                TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32 && ITEMS_AC % NTA == 0 && PA >= RA &&
                                (TPI == 1 || (AG * NZ) % 16 == 0);
 };
@@ -398,31 +398,37 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     // With TPI = 2 the two half-warps share the same 16 items (lane l and
     // l ^ 16, dft_pair), so that each half-warp's accesses stay unit-stride.
     constexpr int TPI = SH::TPI, NV = RB / TPI;
-    const int item = TPI == 2 ? (tid >> 5) * 16 + (tid & 15) : tid;
+    // items per thread: one with a lane pair per item, else as many rounds as needed
+    constexpr int ROUNDS = TPI == 2 ? 1 : (AG * NZ + SH::NTB - 1) / SH::NTB;
+    const int item0 = TPI == 2 ? (tid >> 5) * 16 + (tid & 15) : tid;
     const int h = TPI == 2 ? ((tid >> 4) & 1) : 0;
     __syncthreads();  // wy visible
-    const int zi = item % NZ, al = item / NZ;
-    const bool in_range = item < AG * NZ;  // warp-uniform: items are contiguous in tid
-    const bool valid = in_range && a0 + al < H;
-    if (in_range) {
-        cpx<float> x[NV];
-        const cpx<float>* src = S + tile + (size_t)al * RB * NZ + zi;
+#pragma unroll 1
+    for (int rd = 0; rd < ROUNDS; ++rd) {
+        const int item = item0 + rd * SH::NTB;
+        const int zi = item % NZ, al = item / NZ;
+        const bool in_range = item < AG * NZ;  // warp-uniform: items are contiguous in tid
+        const bool valid = in_range && a0 + al < H;
+        if (in_range) {
+            cpx<float> x[NV];
+            const cpx<float>* src = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-        for (int n1 = 0; n1 < NV; ++n1) {
-            const int jj = TPI * n1 + h;
-            cpx<float> v0 = {0.f, 0.f};
-            if (valid) v0 = src[(size_t)jj * NZ];
-            x[n1] = cmul(v0, wy[jj]);
-        }
-        if constexpr (TPI == 2) {
-            dft_pair<RB, 16>(x, h);
-        } else {
-            Dft<RB, float>::run(x);
-        }
+            for (int n1 = 0; n1 < NV; ++n1) {
+                const int jj = TPI * n1 + h;
+                cpx<float> v0 = {0.f, 0.f};
+                if (valid) v0 = src[(size_t)jj * NZ];
+                x[n1] = cmul(v0, wy[jj]);
+            }
+            if constexpr (TPI == 2) {
+                dft_pair<RB, 16>(x, h);
+            } else {
+                Dft<RB, float>::run(x);
+            }
 #pragma unroll
-        for (int k1 = 0; k1 < NV; ++k1) {
-            const XchgCol<float, CB> col = {xb + al * RB + k1 + h * NV, 0};
-            col[zi] = x[k1];
+            for (int k1 = 0; k1 < NV; ++k1) {
+                const XchgCol<float, CB> col = {xb + al * RB + k1 + h * NV, 0};
+                col[zi] = x[k1];
+            }
         }
     }
     __syncthreads();
@@ -466,22 +472,29 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
 #pragma unroll
     for (int e = 0; e < EZ / 2; ++e) buf[0][t + TFZ * e] = v[0][e];
     __syncthreads();
-    if (in_range) {
-        cpx<float> x[NV];
+#pragma unroll 1
+    for (int rd = 0; rd < ROUNDS; ++rd) {
+        const int item = item0 + rd * SH::NTB;
+        const int zi = item % NZ, al = item / NZ;
+        const bool in_range = item < AG * NZ;
+        const bool valid = in_range && a0 + al < H;
+        if (in_range) {
+            cpx<float> x[NV];
 #pragma unroll
-        for (int n1 = 0; n1 < NV; ++n1) {
-            const XchgCol<float, CB> col = {xb + al * RB + TPI * n1 + h, 0};
-            x[n1] = col[zi];
-        }
-        if constexpr (TPI == 2) {
-            dft_pair<RB, 16>(x, h);
-        } else {
-            Dft<RB, float>::run(x);
-        }
-        if (valid) {
-            cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
+            for (int n1 = 0; n1 < NV; ++n1) {
+                const XchgCol<float, CB> col = {xb + al * RB + TPI * n1 + h, 0};
+                x[n1] = col[zi];
+            }
+            if constexpr (TPI == 2) {
+                dft_pair<RB, 16>(x, h);
+            } else {
+                Dft<RB, float>::run(x);
+            }
+            if (valid) {
+                cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-            for (int k1 = 0; k1 < NV; ++k1) dst[(size_t)(k1 + h * NV) * NZ] = x[k1];
+                for (int k1 = 0; k1 < NV; ++k1) dst[(size_t)(k1 + h * NV) * NZ] = x[k1];
+            }
         }
     }
 }
