@@ -181,6 +181,46 @@ def job_rate(units_per_rank, steps, world, ms_max):
     return world * units_per_rank * steps / (ms_max / 1e3)
 
 
+class CudaClock:
+    """Device time of the work enqueued on `stream` between start() and stop()."""
+
+    def __init__(self, stream):
+        import torch
+
+        self.stream = stream
+        self.a = torch.cuda.Event(enable_timing=True)
+        self.b = torch.cuda.Event(enable_timing=True)
+
+    def start(self):
+        self.a.record(self.stream)
+
+    def stop(self):
+        self.b.record(self.stream)
+
+    def ms(self):
+        return self.a.elapsed_time(self.b)
+
+
+def replica_timing(step, sync, steps, warmup, clock, device=None, during=None):
+    """The timed region every rank runs: `warmup` untimed steps, then exactly
+    `steps` steps on `clock`, with `sync` (barrier over the ranks and the
+    device) on both sides; returns the slowest rank's milliseconds.  `during`
+    is a context manager held around the timed steps (the clock sampler)."""
+    import contextlib
+
+    for _ in range(warmup):
+        step()
+    sync()
+    with (during if during is not None else contextlib.nullcontext()):
+        sync()
+        clock.start()
+        for _ in range(steps):
+            step()
+        clock.stop()
+        sync()
+    return max_over_ranks(clock.ms(), device=device)
+
+
 def result_line(args, world, value, ms_per_step, dtype, config, **extra):
     """The JSON line rank 0 prints (keys of the driver's contract first)."""
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -450,7 +490,7 @@ def reference_arm(args):
 # main
 # ---------------------------------------------------------------------------
 
-def main():
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -459,7 +499,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="skip the single-box rows of the other configs")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -504,18 +544,8 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        start.record(stream)
-        for _ in range(args.steps):
-            step()
-        end.record(stream)
-        barrier()
-    ms = max_over_ranks(start.elapsed_time(end), device=dev)
+    clk = ClockSampler(local)
+    ms = replica_timing(step, barrier, args.steps, args.warmup, CudaClock(stream), device=dev, during=clk)
     ms_per_step = ms / args.steps
     nbox = len(boxes)
     value = job_rate(nbox, args.steps, world, ms)
