@@ -101,8 +101,9 @@ struct SweepShape {
     static constexpr int CB = AG * RB;
     static constexpr int NTB = CB * TFZ;
     static constexpr int NGA = (H + AG - 1) / AG;
-    // threads per y-stage item of pass B (1 or 2: a radix-2 split over a lane pair)
-    static constexpr int TPI = NTB / (AG * NZ) >= 2 && RB % 2 == 0 ? 2 : 1;
+    // threads per y-stage item of pass B: 1 (a lane pair per item, dft_pair,
+    // costs more instructions than it saves in latency: measured slower)
+    static constexpr int TPI = 1;
     static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
     static constexpr int WY_BYTES = (RB * (int)sizeof(cpx<float>) + 15) / 16 * 16;  // ω_NY^{k·j}, j < RB
     static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES + WY_BYTES +
