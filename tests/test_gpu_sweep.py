@@ -202,3 +202,46 @@ def test_sweep_stages_compose_to_the_solve(sbp):
     five = _plan(sbp, box, schedule=1)
     with pytest.raises(sbp.SbpError):
         five.run_stage(sbp.Stage.SWEEP_MIDDLE, None, None)
+
+
+_TUNE_SCRIPT = """
+import sys
+sys.path.insert(0, {root!r})
+import torch
+from paper_2510_10070_gb300 import sbp
+shapes = [(64, 64, 64)] * 3 + [(128, 128, 64)] * 2
+plans = [sbp.Plan(nx, ny, nz, 8.0, 8.0, 4.0, dtype=1) for nx, ny, nz in shapes]
+rhos = [torch.rand((nz, ny, nx), device="cuda") for nx, ny, nz in shapes]
+outs = [torch.empty_like(r) for r in rhos]
+sbp.solve_batched(plans, rhos, outs, [0.1 * i for i in range(len(plans))])
+torch.cuda.synchronize()
+print("launches", sbp.batch_info(plans, rhos, outs)[0])
+"""
+
+
+def test_tuning_choice_is_saved_and_reloaded(tmp_path):
+    # The batched executor's first call times its candidates and appends the
+    # choice to the SBP_TUNE_CACHE file; a later process with the same batch
+    # shapes on the same GPU reads it and skips the timing (SBP_TUNE_LOG shows
+    # which happened).
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "batch.py"
+    script.write_text(_TUNE_SCRIPT.format(root=root))
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, SBP_TUNE_CACHE=str(cache), SBP_TUNE_LOG="1")
+    for k in ("SBP_BATCH_SCHEDULE", "SBP_BATCH_BRANCHES", "SBP_BATCH_CHUNK"):
+        env.pop(k, None)
+    first = subprocess.run([sys.executable, str(script)], env=env, capture_output=True, text=True, timeout=300)
+    assert first.returncode == 0, first.stderr
+    assert "[sbp tune] choice" in first.stderr
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1 and "\t" in lines[0]
+    second = subprocess.run([sys.executable, str(script)], env=env, capture_output=True, text=True, timeout=300)
+    assert second.returncode == 0, second.stderr
+    assert "[sbp tune]" not in second.stderr  # no timing: the saved choice was used
+    assert first.stdout.split()[-1] == second.stdout.split()[-1]
+    assert len(cache.read_text().strip().splitlines()) == 1
