@@ -753,9 +753,35 @@ def main(argv=None):
 
         want3 = torch.from_numpy(O.solve(small, O.SolveParams(sb.Lx, sb.Ly, sb.Lz), W.T_512)).to(dev)
         sd = torch.from_numpy(small).to(dev)
-        side["config3_64x64x64_copy"] = {"fp64_vs_oracle": errors(plan_for(sb, 0).solve(sd, t=W.T_512), want3),
-                                         "fp32_vs_oracle": errors(plan_for(sb, 1).solve(sd.float(), t=W.T_512),
-                                                                  want3)}
+        q64, q32 = plan_for(sb, 0), plan_for(sb, 1)
+        m64, o64 = timed_solve(q64, sd, W.T_512, 20)
+        m32, o32 = timed_solve(q32, sd.float(), W.T_512, 50)
+        side["config3_64x64x64_copy"] = {"fp64": solve_row(sb, m64, 8, peak), "fp32": solve_row(sb, m32, 4, peak),
+                                         "fp64_vs_oracle": errors(o64, want3), "fp32_vs_oracle": errors(o32, want3)}
+        # config 1: 32³ noisy Gaussian (seed 0), t = 0.7, against the oracle;
+        # one box alone is launch-latency bound, so 256 such boxes in one
+        # batched call are timed too
+        b1 = W.BOX_32
+        rho1 = W.noisy_gaussian(b1, seed=0)
+        want1 = torch.from_numpy(O.solve(rho1, O.SolveParams(b1.Lx, b1.Ly, b1.Lz, q=b1.q, Omega=b1.Omega, G=b1.G),
+                                         W.T_32)).to(dev)
+        r1 = torch.from_numpy(rho1).to(dev)
+        q64, q32 = plan_for(b1, 0), plan_for(b1, 1)
+        m64, o64 = timed_solve(q64, r1, W.T_32, 50)
+        m32, o32 = timed_solve(q32, r1.float(), W.T_32, 50)
+        nb1 = 256
+        qs = [plan_for(b1, 1) for _ in range(nb1)]
+        rs = [r1.float().clone() for _ in range(nb1)]
+        fs = [torch.empty_like(r) for r in rs]
+        ts1 = [W.T_32] * nb1
+        mb = event_time_ms(lambda: sbp.solve_batched(qs, rs, fs, ts1, stream=stream), stream, 20, flush=flush)
+        side["config1_32x32x32"] = {"fp64": solve_row(b1, m64, 8, peak), "fp32": solve_row(b1, m32, 4, peak),
+                                    "fp64_vs_oracle": errors(o64, want1), "fp32_vs_oracle": errors(o32, want1),
+                                    f"fp32_batched_{nb1}": {"ms_per_call": mb, "solves_per_s": nb1 / (mb / 1e3),
+                                                            "worst_vs_oracle": worst([errors(f, want1) for f in fs])}}
+        for p in qs:
+            p.close()
+        del q64, q32, qs, rs, fs
         # config 5: 1024×1024×512 clumpy disc (float32 input), t = 3.3
         b5 = W.BOX_1024
         rho5 = W.clumpy_disc(b5, seed=5, device=dev, dtype=np.float32)

@@ -9,10 +9,11 @@
 //   pass A (k3_forward): per (plane group, j ∈ [0, RB)): the real rows
 //       y = j + RB·r (r < RA) of ZA planes are transformed along x (two rows
 //       per complex FFT, Hermitian split on shuffles), then for every (z, a)
-//       the radix-RA stage over r is applied; output k ∈ [0, RA) is stored at
-//       S[k][a][j][z].  The first blocks of the grid fill the Green's table.
-//   pass B (k3_middle): per (k, group of AG columns a): twiddle ω_NY^{k·j}
-//       and the radix-RB stage over j give the full y spectrum at
+//       the radix-RA stage over r is applied and its output k ∈ [0, RA),
+//       times the next stage's twiddle ω_NY^{k·j}, is stored at S[k][a][j][z].
+//       The first blocks of the grid fill the Green's table.
+//   pass B (k3_middle): per (k, group of AG columns a): the radix-RB stage
+//       over j gives the full y spectrum at
 //       b = k + RA·r'; each (b, a) column then takes the padded length-2NZ z
 //       transform, the multiply by 4πG/(NX·NY·2NZ)·Ĝ_eff and the truncated
 //       inverse (as k_z_padded); the inverse y transform's first stage
@@ -91,8 +92,9 @@ struct SweepShape {
     // y-stage items of passes A and C: (plane, a) for a < NX/2, the a = 0 item
     // also carrying the real a = NX/2 column as its imaginary part
     static constexpr int ITEMS_AC = ZA * (NX / 2);
-    // twiddles | exchange / staging / TMA box | pass A: pair sums (PA); pass C: ω_NY^{j·k} (RA) and an mbarrier
-    static constexpr size_t smem_ac = (size_t)(NX + XS) * sizeof(cpx<float>) + (size_t)PA * 8;
+    // twiddles | exchange / staging / TMA box | pass A: pair sums (PA) and ω_NY^{k·j} (RA);
+    // pass C: ω_NY^{j·k} (RA) and an mbarrier
+    static constexpr size_t smem_ac = (size_t)(NX + XS + PA + RA) * sizeof(cpx<float>);
     // pass B: AG columns a, RB y columns each, TFZ threads per padded column
     static constexpr int M = 2 * NZ;
     static constexpr int EZ = plan_E(M, false);
@@ -101,12 +103,14 @@ struct SweepShape {
     static constexpr int CB = AG * RB;
     static constexpr int NTB = CB * TFZ;
     static constexpr int NGA = (H + AG - 1) / AG;
-    // threads per y-stage item of pass B: 1 (a lane pair per item, dft_pair,
-    // costs more instructions than it saves in latency: measured slower)
-    static constexpr int TPI = 1;
+    // y-stage items of pass B, (a, z) with one thread each, in ROUNDS_B
+    // rounds.  (A lane pair per item costs more instructions than it saves in
+    // latency, and so does a table of the Green's factors filled by the
+    // threads a round leaves without an item: both measured slower.)
+    static constexpr int ITEMS_B = AG * NZ;
+    static constexpr int ROUNDS_B = (ITEMS_B + NTB - 1) / NTB;
     static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
-    static constexpr int WY_BYTES = (RB * (int)sizeof(cpx<float>) + 15) / 16 * 16;  // ω_NY^{k·j}, j < RB
-    static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES + WY_BYTES +
+    static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES +
                                      (size_t)xchg_slots<float>(M, CB) * sizeof(cpx<float>);
     // TMA path of passes A and C: the block's box of the half spectrum,
     // [k < RA][a < H][j: 1][z < ZA], moved by one bulk tensor copy through the
@@ -117,8 +121,7 @@ struct SweepShape {
                                 PA >= RA + 1 && (NX * 8) % 128 == 0;
     static constexpr bool ok = RA > 0 && ZA > 0 && (NY % RA) == 0 && (RA % 2) == 0 &&
                                NTA % 32 == 0 && NTA <= 512 && NTB <= 256 && RB * TFZ <= 256 &&
-                               TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32 && ITEMS_AC % NTA == 0 && PA >= RA &&
-                               (TPI == 1 || (AG * NZ) % 16 == 0);
+                               TFZ % 2 == 0 && NTB % 32 == 0 && TFX <= 32 && ITEMS_AC % NTA == 0 && PA >= RA;
 };
 
 // Per-box descriptor of a sweep launch (device memory).
@@ -158,27 +161,6 @@ struct SweepArgs {
     int withhold;           // test switch: the TMA loads arm no copy, so their waits run out
 };
 
-// Radix-R DFT split over a lane pair (lanes l and l ^ LANE_XOR).  Thread h
-// holds x[n1] = in[2 n1 + h], n1 < R/2, and ends with out[k1 + h R/2]:
-//   out[k1 + (R/2) k2] = A0[k1] + (-1)^k2 ω_R^{k1} A1[k1],  A_h = DFT_{R/2}(x of h).
-// Every lane of the warp must take part (the shuffles use the full mask).
-template <int R, int LANE_XOR>
-__device__ __forceinline__ void dft_pair(cpx<float> (&x)[R / 2], int h) {
-    Dft<R / 2, float>::run(x);
-    static_for<1, R / 2>([&](auto kc) {
-        constexpr int k1 = decltype(kc)::value;
-        const cpx<float> w = twiddle_const<R, k1>(x[k1]);
-        x[k1] = h ? w : x[k1];
-    });
-#pragma unroll
-    for (int k1 = 0; k1 < R / 2; ++k1) {
-        cpx<float> o;
-        o.x = __shfl_xor_sync(0xffffffffu, x[k1].x, LANE_XOR);
-        o.y = __shfl_xor_sync(0xffffffffu, x[k1].y, LANE_XOR);
-        x[k1] = h ? csub(o, x[k1]) : cadd(x[k1], o);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // pass A
 // ---------------------------------------------------------------------------
@@ -213,8 +195,10 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     cpx<float>* tw = reinterpret_cast<cpx<float>*>(smem_raw);
     cpx<float>* xb = tw + NX;
     FF* psum = reinterpret_cast<FF*>(xb + XS);
+    cpx<float>* wyk = xb + XS + SH::PA;  // ω_NY^{k·j}, k < RA
     const int tid = threadIdx.x;
     build_stage_twiddles<NX, EX, float>(tw, A.twx);  // the x transform's stage table (fits in NX slots)
+    if (tid < RA) wyk[tid] = A.twy[(tid * j) % NY];
 
     const int t = tid % TFX, c = tid / TFX;
     const int zl = c / (RA / 2), p = c % (RA / 2);
@@ -306,6 +290,8 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
             }
         }
         Dft<RA, float>::run(x);
+        // output k, times the next y stage's twiddle ω_NY^{k·j}
+        auto tw_k = [&](cpx<float> u, int k) { return k == 0 ? u : cmul(u, wyk[k]); };
         if constexpr (SH::TMA) {
             // one round of items: stage the outputs in box order [k][a][zi]
             // (aliasing the staging, hence the barrier) and store the box by TMA
@@ -313,13 +299,13 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
             __syncthreads();
             if (a != 0) {
 #pragma unroll
-                for (int k = 0; k < RA; ++k) bx[(k * H + a) * ZA + zi] = x[k];
+                for (int k = 0; k < RA; ++k) bx[(k * H + a) * ZA + zi] = tw_k(x[k], k);
             } else {
 #pragma unroll
                 for (int k = 0; k < RA; ++k) {
                     const cpx<float> c = x[k], d = x[(RA - k) % RA];
-                    bx[(k * H) * ZA + zi] = {0.5f * (c.x + d.x), 0.5f * (c.y - d.y)};
-                    bx[(k * H + NX / 2) * ZA + zi] = {0.5f * (c.y + d.y), 0.5f * (d.x - c.x)};
+                    bx[(k * H) * ZA + zi] = tw_k({0.5f * (c.x + d.x), 0.5f * (c.y - d.y)}, k);
+                    bx[(k * H + NX / 2) * ZA + zi] = tw_k({0.5f * (c.y + d.y), 0.5f * (d.x - c.x)}, k);
                 }
             }
             fence_proxy_async_smem();
@@ -334,14 +320,14 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
         cpx<float>* dst = S + ((size_t)a * RB + j) * NZ + z0 + zi;
         if (a != 0) {
 #pragma unroll
-            for (int k = 0; k < RA; ++k) dst[k * KS] = x[k];
+            for (int k = 0; k < RA; ++k) dst[k * KS] = tw_k(x[k], k);
         } else {
             cpx<float>* dstN = S + ((size_t)(NX / 2) * RB + j) * NZ + z0 + zi;
 #pragma unroll
             for (int k = 0; k < RA; ++k) {
                 const cpx<float> c = x[k], d = x[(RA - k) % RA];
-                dst[k * KS] = {0.5f * (c.x + d.x), 0.5f * (c.y - d.y)};
-                dstN[k * KS] = {0.5f * (c.y + d.y), 0.5f * (d.x - c.x)};
+                dst[k * KS] = tw_k({0.5f * (c.x + d.x), 0.5f * (c.y - d.y)}, k);
+                dstN[k * KS] = tw_k({0.5f * (c.y + d.y), 0.5f * (d.x - c.x)}, k);
             }
         }
     }
@@ -361,8 +347,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<float>* twM = reinterpret_cast<cpx<float>*>(smem_raw);
     GreenT<float>* gm = reinterpret_cast<GreenT<float>*>(twM + M);
-    cpx<float>* wy = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
-    cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(wy) + SH::WY_BYTES);
+    cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
     const int tid = threadIdx.x;
     if (blockIdx.x == 0) {
         // the FP64 mean mode: vk0[i] = coef Σ_j c00[i - j + NZ - 1] S[j] from the
@@ -383,7 +368,6 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     const int k = ((int)blockIdx.x - 1) / NGA, ag = ((int)blockIdx.x - 1) % NGA;
     const int a0 = ag * AG;
     for (int i = tid; i < M; i += SH::NTB) twM[i] = A.twM[i];
-    if (tid < RB) wy[tid] = A.twy[(k * tid) % NY];
     if (tid < CB) {
         const int a = a0 + tid / RB, b = k + RA * (tid % RB);
         GreenT<float> g = {};
@@ -394,40 +378,33 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     }
     cpx<float>* __restrict__ S = B.S;
     const size_t tile = ((size_t)k * H + a0) * RB * NZ;  // this block's [AG][RB][NZ] tile
-    // y stage 2 (forward): item (al, z) takes twiddle ω_NY^{k·j} and the
-    // radix-RB DFT over j; output r' is column al·RB + r' (b = k + RA·r').
-    // With TPI = 2 the two half-warps share the same 16 items (lane l and
-    // l ^ 16, dft_pair), so that each half-warp's accesses stay unit-stride.
-    constexpr int TPI = SH::TPI, NV = RB / TPI;
-    // items per thread: one with a lane pair per item, else as many rounds as needed
-    constexpr int ROUNDS = TPI == 2 ? 1 : (AG * NZ + SH::NTB - 1) / SH::NTB;
-    const int item0 = TPI == 2 ? (tid >> 5) * 16 + (tid & 15) : tid;
-    const int h = TPI == 2 ? ((tid >> 4) & 1) : 0;
-    __syncthreads();  // wy visible
+    const float scale = (float)B.scale;
+    const float kzc = (float)B.kzc;
+    const float L2half = (float)(0.5 * B.L * B.L);
+    __syncthreads();  // gm visible
+    // y stage 2 (forward): item (al, z) takes the radix-RB DFT over j (its
+    // twiddle ω_NY^{k·j} came with pass A's output); output r' is column
+    // al·RB + r' (b = k + RA·r').
+    constexpr int ROUNDS = SH::ROUNDS_B;
 #pragma unroll 1
     for (int rd = 0; rd < ROUNDS; ++rd) {
-        const int item = item0 + rd * SH::NTB;
+        const int item = tid + rd * SH::NTB;
         const int zi = item % NZ, al = item / NZ;
-        const bool in_range = item < AG * NZ;  // warp-uniform: items are contiguous in tid
+        const bool in_range = item < SH::ITEMS_B;  // warp-uniform: items are contiguous in tid
         const bool valid = in_range && a0 + al < H;
         if (in_range) {
-            cpx<float> x[NV];
+            cpx<float> x[RB];
             const cpx<float>* src = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-            for (int n1 = 0; n1 < NV; ++n1) {
-                const int jj = TPI * n1 + h;
+            for (int n1 = 0; n1 < RB; ++n1) {
                 cpx<float> v0 = {0.f, 0.f};
-                if (valid) v0 = src[(size_t)jj * NZ];
-                x[n1] = cmul(v0, wy[jj]);
+                if (valid) v0 = src[(size_t)n1 * NZ];
+                x[n1] = v0;
             }
-            if constexpr (TPI == 2) {
-                dft_pair<RB, 16>(x, h);
-            } else {
-                Dft<RB, float>::run(x);
-            }
+            Dft<RB, float>::run(x);
 #pragma unroll
-            for (int k1 = 0; k1 < NV; ++k1) {
-                const XchgCol<float, CB> col = {xb + al * RB + k1 + h * NV, 0};
+            for (int k1 = 0; k1 < RB; ++k1) {
+                const XchgCol<float, CB> col = {xb + al * RB + k1, 0};
                 col[zi] = x[k1];
             }
         }
@@ -442,10 +419,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     for (int e = 0; e < EZ / 2; ++e) v[0][e] = buf[0][t + TFZ * e];
     fft_static_padded<M, EZ, 1, float>(v, t, twM, buf);  // starts with a barrier
     {
-        const float scale = (float)B.scale;
         const GreenCoef<float> q = green_coef<float>(gm[c], scale, true);
-        const float kzc = (float)B.kzc;
-        const float L2half = (float)(0.5 * B.L * B.L);
         static_assert(TFZ % 2 == 0 && (CB * TFZ) % 32 == 0, "padded z shape");
         if (__all_sync(0xffffffffu, q.same && !q.kzero)) {
             const float num = (t & 1) ? q.ao : q.ae;
@@ -475,26 +449,22 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     __syncthreads();
 #pragma unroll 1
     for (int rd = 0; rd < ROUNDS; ++rd) {
-        const int item = item0 + rd * SH::NTB;
+        const int item = tid + rd * SH::NTB;
         const int zi = item % NZ, al = item / NZ;
-        const bool in_range = item < AG * NZ;
+        const bool in_range = item < SH::ITEMS_B;
         const bool valid = in_range && a0 + al < H;
         if (in_range) {
-            cpx<float> x[NV];
+            cpx<float> x[RB];
 #pragma unroll
-            for (int n1 = 0; n1 < NV; ++n1) {
-                const XchgCol<float, CB> col = {xb + al * RB + TPI * n1 + h, 0};
+            for (int n1 = 0; n1 < RB; ++n1) {
+                const XchgCol<float, CB> col = {xb + al * RB + n1, 0};
                 x[n1] = col[zi];
             }
-            if constexpr (TPI == 2) {
-                dft_pair<RB, 16>(x, h);
-            } else {
-                Dft<RB, float>::run(x);
-            }
+            Dft<RB, float>::run(x);
             if (valid) {
                 cpx<float>* dst = S + tile + (size_t)al * RB * NZ + zi;
 #pragma unroll
-                for (int k1 = 0; k1 < NV; ++k1) dst[(size_t)(k1 + h * NV) * NZ] = x[k1];
+                for (int k1 = 0; k1 < RB; ++k1) dst[(size_t)k1 * NZ] = x[k1];
             }
         }
     }
