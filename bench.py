@@ -653,6 +653,23 @@ def main(argv=None):
                     "note": "FP32 batch output of the timed step; the FP64 GPU solves are pinned to the FP64 "
                             "oracle at <= 1e-12 rel-L2 by the test suite"}
 
+    # ---- the same batch in FP64 through one batched call per step (the
+    # precision of the accuracy reference), for the FP32/FP64 speed ratio
+    batch_fp64 = None
+    if args.workload == "batch96" and rank == 0 and not args.no_side:
+        plans64 = [sbp.Plan(b.nx, b.ny, b.nz, b.Lx, b.Ly, b.Lz, q=b.q, Omega=b.Omega, G=b.G, dtype=0) for b in boxes]
+        r64 = [r.double() for r in rhos]
+        f64 = [torch.empty_like(r) for r in r64]
+        m64 = event_time_ms(lambda: sbp.solve_batched(plans64, r64, f64, times, stream=stream), stream, 3)
+        b64 = sum(alg_bytes(b, 8) for b in boxes)
+        batch_fp64 = {"ms_per_step": m64, "solves_per_s": nbox / (m64 / 1e3),
+                      "alg_gbs": b64 / (m64 / 1e3) / 1e9, "hbm_frac": b64 / (m64 / 1e3) / 1e9 / peak,
+                      "fp32_over_fp64_speed": m64 / ms_per_step,
+                      "fp32_vs_fp64_batch_worst_box": worst([errors(phis[i], f64[i]) for i in range(nbox)])}
+        for p in plans64:
+            p.close()
+        del plans64, r64, f64
+
     # ---- dominant kernel: the middle sweep of the largest shape, launched for
     # all boxes of that shape at once as the batch graph runs it (the padded z
     # pass of one box where that shape runs five passes), timed alone with
@@ -872,7 +889,7 @@ def main(argv=None):
                            e2e={"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                                 "d2h_bytes_per_step": h2d},
                            gpu_launches=launches_per_step * args.steps,
-                           clocks=clk.summary(), accuracy=accuracy, single_box=side)
+                           clocks=clk.summary(), accuracy=accuracy, batch_fp64=batch_fp64, single_box=side)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
