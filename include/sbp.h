@@ -333,15 +333,19 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  * The three sweeps of a plan whose solves run them (SBP_OPT_SCHEDULE), on the
  * plan's own workspace in its internal layout (else SBP_ERR_INVALID_ARG):
  *   SBP_STAGE_SWEEP_FORWARD: in = real [nz][ny][nx]; out ignored (may be
- *                         NULL).  Fills the Green's table for time t and the
- *                         plane sums, and leaves the x transform and the
- *                         first y stage in the workspace.
+ *                         NULL).  Computes the plane sums and leaves the x
+ *                         transform and the first y stage (with the second
+ *                         stage's twiddles) in the workspace; for most shapes
+ *                         it also fills the Green's table for time t.
  *   SBP_STAGE_SWEEP_MIDDLE:  in and out ignored.  The second y stage, the
  *                         padded z pass with the Green's multiply and the
  *                         first inverse y stage, in place, plus the FP64
- *                         mean mode.
+ *                         mean mode.  Where the forward stage fills no table
+ *                         (256-wide shapes), it evaluates the Green's
+ *                         parameters for time t itself.
  *   SBP_STAGE_SWEEP_INVERSE: in ignored; out = real [nz][ny][nx].
- * Run in this order they give sbp_solve's result bit for bit.
+ * Run in this order with the same t they give sbp_solve's result bit for
+ * bit.
  */
 sbp_status sbp_run_stage(sbp_plan p, int stage, const void* in, void* out, double t, void* stream);
 

@@ -1082,7 +1082,7 @@ bool configure_sweep(sbp_plan_s* p) {
         }
     }
     p->sk = k;
-    p->sweep_green_blocks = (p->h * p->ny + k.nta - 1) / k.nta;
+    p->sweep_green_blocks = k.green_mid ? 0 : (p->h * p->ny + k.nta - 1) / k.nta;
     p->sweep = true;
     return true;
 }

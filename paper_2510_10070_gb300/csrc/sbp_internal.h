@@ -242,6 +242,7 @@ struct SweepKernels {
     void (*inv)(SweepArgs) = nullptr;
     int nta = 0, ntb = 0, za = 0, ra = 0, rb = 0, nga = 0;
     size_t smem_ac = 0, smem_b = 0;
+    bool green_mid = false;  // pass B evaluates the Green's parameters itself (no table fill in pass A)
 };
 #define SBP_SWEEP_LIST(X) X(32, 32, 32) X(64, 64, 32) X(64, 64, 64) X(128, 128, 64) X(128, 128, 128) \
     X(192, 192, 96) X(256, 256, 64) X(256, 256, 128)
@@ -262,6 +263,7 @@ SBP_SWEEP_LIST(SBP_DECLARE_SWEEP)
         k.nga = SH::NGA;                               \
         k.smem_ac = SH::smem_ac;                       \
         k.smem_b = SH::smem_b;                         \
+        k.green_mid = SH::GREEN_MID;                   \
         return k;                                      \
     }
 

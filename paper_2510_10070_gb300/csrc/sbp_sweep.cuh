@@ -109,6 +109,15 @@ struct SweepShape {
     // threads a round leaves without an item: both measured slower.)
     static constexpr int ITEMS_B = AG * NZ;
     static constexpr int ROUNDS_B = (ITEMS_B + NTB - 1) / NTB;
+    // When the one round of items leaves at least CB threads idle, CB of them
+    // (from G0 on) evaluate the block's Green's parameters in FP64 meanwhile,
+    // and pass A fills no table (GREEN_MID: 256² saves pass A's table blocks,
+    // 28 µs of 264 for 16 boxes, against 7 µs more in pass B).  Otherwise pass
+    // A's leading blocks fill the table and pass B reads it (with a second
+    // round, as at 192², the FP64 work lands on the critical path: measured
+    // slower).
+    static constexpr int G0 = ITEMS_B - (ROUNDS_B - 1) * NTB;
+    static constexpr bool GREEN_MID = ROUNDS_B == 1 && NTB - G0 >= CB;
     static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
     static constexpr size_t smem_b = (size_t)M * sizeof(cpx<float>) + GM_BYTES +
                                      (size_t)xchg_slots<float>(M, CB) * sizeof(cpx<float>);
@@ -368,20 +377,28 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     const int k = ((int)blockIdx.x - 1) / NGA, ag = ((int)blockIdx.x - 1) % NGA;
     const int a0 = ag * AG;
     for (int i = tid; i < M; i += SH::NTB) twM[i] = A.twM[i];
-    if (tid < CB) {
-        const int a = a0 + tid / RB, b = k + RA * (tid % RB);
-        GreenT<float> g = {};
+    // the Green's parameters of column c: mode (a, b), a = a0 + c / RB, b = k + RA·(c % RB)
+    auto column_mode = [&](int c, GreenT<float>& g) {
+        const int a = a0 + c / RB, b = k + RA * (c % RB);
+        g = GreenT<float>{};
         g.kzero = 1;  // columns past the half spectrum: finite, never stored
         g.same = 1;
-        if (a < H) g = B.green[(size_t)b * H + a];
-        gm[tid] = g;
+        return a < H ? (size_t)b * H + a : (size_t)-1;
+    };
+    if constexpr (!SH::GREEN_MID) {
+        if (tid < CB) {
+            GreenT<float> g;
+            const size_t q = column_mode(tid, g);
+            if (q != (size_t)-1) g = B.green[q];
+            gm[tid] = g;
+        }
     }
     cpx<float>* __restrict__ S = B.S;
     const size_t tile = ((size_t)k * H + a0) * RB * NZ;  // this block's [AG][RB][NZ] tile
     const float scale = (float)B.scale;
     const float kzc = (float)B.kzc;
     const float L2half = (float)(0.5 * B.L * B.L);
-    __syncthreads();  // gm visible
+    __syncthreads();  // the setup copies done
     // y stage 2 (forward): item (al, z) takes the radix-RB DFT over j (its
     // twiddle ω_NY^{k·j} came with pass A's output); output r' is column
     // al·RB + r' (b = k + RA·r').
@@ -407,6 +424,22 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
                 const XchgCol<float, CB> col = {xb + al * RB + k1, 0};
                 col[zi] = x[k1];
             }
+        }
+    }
+    if constexpr (SH::GREEN_MID) {
+        // FP64 evaluation of the block's CB modes (the table's values: |k(t)|²
+        // and 1 - e^{-|k|L}, rounded once to float) by threads the last round
+        // left without an item, on the otherwise idle FP64 pipe
+        const int c = tid - SH::G0;
+        if (c >= 0 && c < CB) {
+            GreenT<float> g;
+            const size_t q = column_mode(c, g);
+            if (q != (size_t)-1) {
+                const double sh = A.rho != nullptr ? (A.s_dev != nullptr ? *A.s_dev : A.s) : *B.s_dev;
+                const GreenMode m = green_mode(a0 + c / RB, k + RA * (c % RB), NX, NY, B.Lx, B.Ly, B.L, sh);
+                g = GreenT<float>{(float)m.k2a, (float)m.omEa, (float)m.k2b, (float)m.omEb, m.kzero, m.same};
+            }
+            gm[c] = g;
         }
     }
     __syncthreads();
