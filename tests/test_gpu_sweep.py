@@ -186,12 +186,16 @@ def test_nyquist_planes_sheared(sbp, shape, dtype):
             parity(got, want, TOL[dtype])
 
 
-def test_sweep_stages_compose_to_the_solve(sbp):
+@pytest.mark.parametrize("shape", [(128, 128, 64), (256, 256, 64)], ids=["table", "green_in_middle"])
+def test_sweep_stages_compose_to_the_solve(sbp, shape):
+    # 128x128x64: the forward sweep fills the Green's table; 256x256x64: the
+    # middle sweep evaluates the Green's parameters at t itself
     import torch
 
-    box = W.Box(128, 128, 64, 8.0, 8.0, 4.0)
+    nx, ny, nz = shape
+    box = W.Box(nx, ny, nz, 8.0, 8.0, 4.0)
     plan = _plan(sbp, box, schedule=2)
-    rho = to_dev(np.random.default_rng(8).standard_normal((64, 128, 128)) + 1.0, 1)
+    rho = to_dev(np.random.default_rng(8).standard_normal((nz, ny, nx)) + 1.0, 1)
     want = plan.solve(rho, t=3.1)
     out = torch.empty_like(rho)
     plan.run_stage(sbp.Stage.SWEEP_FORWARD, rho, None, t=3.1)
