@@ -38,9 +38,15 @@
 namespace sbp {
 
 // Radix of the y stage fused into the x passes (RA) for a length NY; the
-// other stage (pass B) has radix NY / RA.  0: no split built for NY.
+// other stage (pass B) has radix NY / RA.  0: no split built for NY.  At 192
+// the split is 12 × 16 with 12-element x transforms (RA·TFX = NX keeps passes
+// A and C at one item round, the TMA path): 384-thread blocks then fit three
+// per SM, and pass B's one round of items leaves threads for the Green's
+// parameters (24 × 8 with 24-element x transforms, two blocks per SM: the
+// 192² group's pass A 148 µs against 130).  (The 192-wide sweeps are built for
+// 192×192×96, where NX = NY.)
 __host__ __device__ constexpr int sweep_ra(int NY) {
-    return NY == 32 ? 4 : NY == 64 ? 8 : NY == 96 ? 12 : NY == 128 ? 16 : NY == 192 ? 24 : NY == 256 ? 16 : 0;
+    return NY == 32 ? 4 : NY == 64 ? 8 : NY == 96 ? 12 : NY == 128 ? 16 : NY == 192 ? 12 : NY == 256 ? 16 : 0;
 }
 
 __host__ __device__ constexpr int sweep_stage_pitch(int need, int ZA) {
@@ -70,8 +76,9 @@ __host__ __device__ constexpr int sweep_za(int NZ, int per) {
 }
 
 // Resident blocks per SM the passes A and C aim for: 512-thread blocks two
-// (64 registers), smaller ones as many as fit 64 registers (or 8).
-__host__ __device__ constexpr int sweep_ac_blocks(int nt) { return nt > 256 ? 2 : (nt <= 128 ? 8 : 4); }
+// (64 registers), 384-thread blocks three (56), smaller ones as many as fit
+// 64 registers (or 8).
+__host__ __device__ constexpr int sweep_ac_blocks(int nt) { return nt > 384 ? 2 : nt > 256 ? 3 : (nt <= 128 ? 8 : 4); }
 
 template <int NX, int NY, int NZ>
 struct SweepShape {
@@ -79,7 +86,7 @@ struct SweepShape {
     static constexpr int RB = RA > 0 ? NY / RA : 1;
     static constexpr int H = NX / 2 + 1;
     // pass A and C: row pairs of ZA planes, TFX threads per pair
-    static constexpr int EX = plan_E(NX, false);
+    static constexpr int EX = NX == 192 ? 12 : plan_E(NX, false);  // see sweep_ra
     static constexpr int TFX = NX / EX;
     static constexpr int ZA = sweep_za(NZ, (RA / 2) * TFX);
     static constexpr int PA = ZA * RA / 2;
