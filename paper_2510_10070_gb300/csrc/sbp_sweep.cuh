@@ -11,7 +11,8 @@
 //       per complex FFT, Hermitian split on shuffles), then for every (z, a)
 //       the radix-RA stage over r is applied and its output k ∈ [0, RA),
 //       times the next stage's twiddle ω_NY^{k·j}, is stored at S[k][a][j][z].
-//       The first blocks of the grid fill the Green's table.
+//       Unless pass B evaluates the Green's parameters itself (GREEN_MID),
+//       the first blocks of the grid fill the Green's table.
 //   pass B (k3_middle): per (k, group of AG columns a): the radix-RB stage
 //       over j gives the full y spectrum at
 //       b = k + RA·r'; each (b, a) column then takes the padded length-2NZ z
