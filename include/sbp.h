@@ -341,7 +341,7 @@ sbp_status sbp_plan_info(sbp_plan p, int* nx, int* ny, int* nz, int* dtype,
  *                         padded z pass with the Green's multiply and the
  *                         first inverse y stage, in place, plus the FP64
  *                         mean mode.  Where the forward stage fills no table
- *                         (256-wide shapes), it evaluates the Green's
+ *                         (192- and 256-wide shapes), it evaluates the Green's
  *                         parameters for time t itself.
  *   SBP_STAGE_SWEEP_INVERSE: in ignored; out = real [nz][ny][nx].
  * Run in this order with the same t they give sbp_solve's result bit for

@@ -120,10 +120,10 @@ struct SweepShape {
     // When the one round of items leaves at least CB threads idle, CB of them
     // (from G0 on) evaluate the block's Green's parameters in FP64 meanwhile,
     // and pass A fills no table (GREEN_MID: 256² saves pass A's table blocks,
-    // 28 µs of 264 for 16 boxes, against 7 µs more in pass B).  Otherwise pass
-    // A's leading blocks fill the table and pass B reads it (with a second
-    // round, as at 192², the FP64 work lands on the critical path: measured
-    // slower).
+    // 28 µs of 264 for 16 boxes, against 7 µs more in pass B; 192² qualifies
+    // with its 12 × 16 split).  Otherwise pass A's leading blocks fill the
+    // table and pass B reads it (with a second round of items the FP64 work
+    // lands on the critical path: measured slower).
     static constexpr int G0 = ITEMS_B - (ROUNDS_B - 1) * NTB;
     static constexpr bool GREEN_MID = ROUNDS_B == 1 && NTB - G0 >= CB;
     static constexpr int GM_BYTES = (CB * (int)sizeof(GreenT<float>) + 15) / 16 * 16;
