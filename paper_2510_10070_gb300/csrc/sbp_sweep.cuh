@@ -406,10 +406,10 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     const float scale = (float)B.scale;
     const float kzc = (float)B.kzc;
     const float L2half = (float)(0.5 * B.L * B.L);
-    __syncthreads();  // the setup copies done
     // y stage 2 (forward): item (al, z) takes the radix-RB DFT over j (its
     // twiddle ω_NY^{k·j} came with pass A's output); output r' is column
-    // al·RB + r' (b = k + RA·r').
+    // al·RB + r' (b = k + RA·r').  It neither reads nor writes what the setup
+    // above writes, so the barrier after it serves both.
     constexpr int ROUNDS = SH::ROUNDS_B;
 #pragma unroll 1
     for (int rd = 0; rd < ROUNDS; ++rd) {
@@ -483,8 +483,10 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     }
     fft_static<M, EZ, 0, 1, float>(v, t, twM, buf);
     // v[e] (e < EZ/2) is the conjugate of the convolved column at z = t + TFZ·e:
-    // exactly the input the inverse y transform's first stage wants
-    __syncthreads();
+    // exactly the input the inverse y transform's first stage wants.  The
+    // transform's last exchange read of this thread was buf[t + TFZ·e] for
+    // every e, slots no other thread reads after that exchange's barrier, so
+    // writing them back needs no barrier first.
 #pragma unroll
     for (int e = 0; e < EZ / 2; ++e) buf[0][t + TFZ * e] = v[0][e];
     __syncthreads();
