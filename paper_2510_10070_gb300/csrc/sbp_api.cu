@@ -1111,6 +1111,10 @@ sbp_status launch_sweep(const sbp_plan_s* p, const SweepArgs& a, int nbox, cudaS
     return launch_status();
 }
 
+// One box: the middle and inverse sweeps are launched with programmatic
+// stream serialisation, so that each launches during the previous sweep's
+// last (partly empty) wave and its blocks wait on griddepcontrol for that
+// sweep's results instead of for the launch.
 sbp_status solve_sweep(const sbp_plan_s* p, const void* rho, void* phi, double t, cudaStream_t st,
                        const double* s_dev) {
     SweepArgs a = sweep_args(p);
@@ -1118,7 +1122,25 @@ sbp_status solve_sweep(const sbp_plan_s* p, const void* rho, void* phi, double t
     a.phi = static_cast<float*>(phi);
     a.s = shear_s(p, t);
     a.s_dev = s_dev;
-    return launch_sweep(p, a, 1, st);
+    const SweepKernels& k = p->sk;
+    const int ablocks = (p->nz / k.za) * k.rb;
+    k.fwd<<<dim3((unsigned)(a.green_blocks + ablocks)), k.nta, k.smem_ac, st>>>(a);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(k.ra * k.nga + 1));
+    cfg.blockDim = dim3((unsigned)k.ntb);
+    cfg.dynamicSmemBytes = k.smem_b;
+    if (cudaLaunchKernelEx(&cfg, k.mid, a) != cudaSuccess) return launch_status();
+    cfg.gridDim = dim3((unsigned)ablocks);
+    cfg.blockDim = dim3((unsigned)k.nta);
+    cfg.dynamicSmemBytes = k.smem_ac;
+    if (cudaLaunchKernelEx(&cfg, k.inv, a) != cudaSuccess) return launch_status();
+    return launch_status();
 }
 
 // Kernels one solve launches (solve_t's dispatch; chunk < 0: the plan's own;

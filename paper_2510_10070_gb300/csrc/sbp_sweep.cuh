@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     constexpr int RP = SH::RP, SP = SH::SP, XS = SH::XS;
     static_assert(SH::ok, "sweep shape");
     const SweepBox& B = A.boxes[blockIdx.y];
+    grid_dep_launch();  // a single solve's middle sweep may launch during this grid's last wave
     if ((int)blockIdx.x < A.green_blocks) {  // Green's table, off the transform blocks
         GreenFill gf;
         gf.tab = B.green;
@@ -366,6 +367,8 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTB, (SweepShape<NX, N
     GreenT<float>* gm = reinterpret_cast<GreenT<float>*>(twM + M);
     cpx<float>* xb = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(gm) + SH::GM_BYTES);
     const int tid = threadIdx.x;
+    grid_dep_launch();  // likewise the inverse sweep
+    grid_dep_wait();    // pass A's spectrum, table and plane sums complete (single solves)
     if (blockIdx.x == 0) {
         // the FP64 mean mode: vk0[i] = coef Σ_j c00[i - j + NZ - 1] S[j] from the
         // plane sums (O(NZ²) at GB300's 1/64-rate FP64: the first block of each
@@ -534,6 +537,7 @@ __global__ void __launch_bounds__(SweepShape<NX, NY, NZ>::NTA, sweep_ac_blocks(S
     const int tid = threadIdx.x;
     cpx<float>* wy = xb + SH::XS;  // ω_NY^{j·k}, k < RA (PA ≥ RA slots after the staging)
     uint64_t* bar = reinterpret_cast<uint64_t*>(wy + RA);
+    grid_dep_wait();  // pass B's spectrum and mean mode complete (single solves)
     if constexpr (SH::TMA) {
         // the block's box [k][a][j][z0 .. z0+ZA) of the half spectrum by one TMA load
         if (tid == 0) {

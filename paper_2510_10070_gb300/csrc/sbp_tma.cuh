@@ -93,6 +93,14 @@ __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.w
 // Make this thread's shared-memory writes visible to the asynchronous (TMA) proxy.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel on its stream still
+// runs; grid_dep_wait blocks until that kernel has completed and its memory
+// is visible, grid_dep_launch lets the next such kernel start launching.
+// Both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Device-side status and debug switches shared by the TMA kernels.
 struct TmaCtl {
     int* err;            // set to 1 when a bounded wait gives up
